@@ -1,0 +1,184 @@
+/*
+ * vmc.h -- C ABI of the GB300 sparse determinant-ratio engine.
+ *
+ * The engine computes, for single-electron variational Monte Carlo moves, the
+ * determinant ratio of successive Slater matrices
+ *     det(A') / det(A) = 1 + u^T A^{-1} e_i ,   u = a' - a_i
+ * (Ahuja, Clark, de Sturler, Ceperley, Kim, "Improved Scaling for Quantum Monte
+ * Carlo on Insulators": Sec. 1 Eq. 2; Sec. 3 Eqs. 11-13) by solving A z = e_i with
+ * right-preconditioned GMRES (Sec. 3.2 Eq. 15), the preconditioner being ILUTP
+ * (Sec. 3.2 Eq. 14; Sec. 4) of a geometrically reordered matrix (Sec. 3.1, the
+ * greedy particle/orbital algorithm), cheaply updated after every accepted move
+ * (Sec. 3.2 Eqs. 16-18), with the effective-stability monitor N of Sec. 3.1 Eq. 10
+ * deciding when to reorder and refactor (Sec. 4).
+ *
+ * Conventions for every call:
+ *   - Pointers are plain host pointers unless the name says "_dev" (device).
+ *   - Host inputs are copied before the call returns; host outputs are written
+ *     before it returns (the call synchronises its stream when it copies to host).
+ *   - The context owns all device memory it allocates; vmc_destroy frees it.
+ *   - Errors are returned as vmc_status; nothing aborts, throws or traps across
+ *     the ABI.  vmc_last_error() describes the most recent failure.
+ *   - Particle ids k and walker ids are the caller's (original) labels; the
+ *     reorderings are internal.
+ *   - A context is not thread-safe; calls on one context must be serialised.
+ */
+#ifndef VMC_H
+#define VMC_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vmc_ctx vmc_ctx; /* opaque */
+
+typedef enum {
+  VMC_OK = 0,
+  VMC_ERR_INVALID = 1,   /* bad argument or size                                  */
+  VMC_ERR_CUDA = 2,      /* a CUDA runtime call failed                             */
+  VMC_ERR_OOM = 3,       /* device allocation failed                               */
+  VMC_ERR_NOCONV = 4,    /* GMRES did not converge after reorder + restarts        */
+  VMC_ERR_BREAKDOWN = 5, /* singular Slater matrix or unusable factorisation       */
+  VMC_ERR_TIMEOUT = 6,   /* a bounded device wait ran out                          */
+  VMC_ERR_STATE = 7,     /* call out of order (e.g. vmc_accept without vmc_ratio)  */
+  VMC_ERR_CAPACITY = 8   /* a fixed device capacity was exceeded                   */
+} vmc_status;
+
+/* One walker's physical system (Sec. 2.1 Eq. 3; Sec. 4).
+ * Sites: simple cubic Z = a (x, y, z), x, y, z in [0, K), numbered
+ * j = x + K (y + K z); body-centred cubic adds a (x+1/2, y+1/2, z+1/2) as j = 2 cell + 1
+ * (corner j = 2 cell).  Orbitals phi_j(r) = exp(-kappa |r - Z_j|^2) when the
+ * minimum-image distance is <= r_c, else 0.  Box side L = K a, periodic.
+ * Requires r_c < L/2 and r_c larger than the lattice's covering radius. */
+typedef struct {
+  int K;          /* cells per side (>= 2)                     */
+  int lattice;    /* 0 = simple cubic (n = K^3), 1 = bcc (2K^3) */
+  double a;       /* lattice constant                          */
+  double kappa;   /* Gaussian decay rate                       */
+  double r_c;     /* orbital cutoff radius                     */
+} vmc_system;
+
+enum { VMC_PREC_FP64 = 0, VMC_PREC_MIXED = 1 };
+enum {
+  VMC_ENGINE_PLAIN = 0,      /* one walker per launch, one launch per move step      */
+  VMC_ENGINE_STEP = 1,       /* one launch per move step advancing every walker      */
+  VMC_ENGINE_PERSISTENT = 2, /* one launch per sweep, every walker (CTA per walker)  */
+  VMC_ENGINE_DENSE_SM = 3    /* explicit inverse + Sherman-Morrison (Sec. 1), FP64   */
+};
+
+/* Solver parameters.  vmc_default_params() fills the defaults noted here. */
+typedef struct {
+  double drop_tol;     /* ILUTP drop tolerance tau, relative to ||a_i||_2 (1e-4)         */
+  double permtol;      /* ILUTP column-pivot tolerance: swap when permtol|w_j| > |w_i| (0.5) */
+  int lfil_extra;      /* extra entries kept per L and per U row; < 0: ceil(avg nnz/row / 2) (-1) */
+  int gmres_m;         /* Krylov dimension per inner solve, <= 40 (30)                   */
+  int max_restarts;    /* extra refinement passes allowed after a failed solve (10)      */
+  double inner_rtol;   /* inner GMRES relative tolerance; <= 0: 1e-10 FP64, 1e-5 mixed (0) */
+  double ratio_tol;    /* goal: predicted relative ratio error (1e-12)                   */
+  double N_max;        /* reorder + refactor when the stability monitor N exceeds it (100) */
+  double slow_factor;  /* ... or when the iterations reach slow_factor x the average (4)  */
+  int max_updates;     /* refactor after this many rank-one preconditioner updates (32)   */
+  int precision;       /* VMC_PREC_FP64 or VMC_PREC_MIXED (MIXED)                         */
+  int engine;          /* VMC_ENGINE_* (PERSISTENT)                                        */
+  int block_threads;   /* threads per walker CTA: 64..512, multiple of 32; 0 = auto (0)  */
+  int sm_refresh;      /* dense engine: fresh inverse every sm_refresh sweeps (1)          */
+} vmc_solver_params;
+
+/* Per-walker statistics (Sec. 4 Tables 2 and 3 analogues). */
+typedef struct {
+  int64_t proposals, accepts;
+  int64_t solves;            /* linear solves started (one per ratio, plus re-solves)      */
+  int64_t inner_iterations;  /* GMRES iterations over all passes                           */
+  int64_t first_pass_iterations; /* iterations of the first pass (the paper's k1 count)    */
+  int64_t outer_passes;      /* FP64 refinement passes                                      */
+  int64_t reorders;          /* reorder + refactor events (all causes)                      */
+  int64_t reorder_monitor, reorder_noconv, reorder_slow, reorder_breakdown;
+  int64_t refactors_updates; /* refactorisations because max_updates was reached           */
+  int64_t factorizations;    /* all ILUTP factorisations                                   */
+  int64_t pivots;            /* ILUTP column swaps in the last factorisation               */
+  double N_max_seen, N_sum;  /* stability monitor: max and sum over solves                 */
+  double nnz_A, nnz_LU;      /* nonzeros of A and of L+U at the last factorisation         */
+  int levels_L, levels_U;    /* triangular-solve level counts at the last factorisation    */
+  int n_updates;             /* current length of the update chain                         */
+  int status;                /* vmc_status of this walker (sticky)                          */
+  int64_t its_hist[64];      /* histogram of first-pass iterations (last bin: >= 63)       */
+} vmc_stats;
+
+/* Fill p with the defaults above. */
+vmc_status vmc_default_params(vmc_solver_params* p);
+
+/* Create a context for n_walkers walkers; systems[w] is walker w's system
+ * (walkers may differ in size: an uneven batch).  stream: a cudaStream_t (or NULL
+ * for the default stream) on which every device operation of the context runs.
+ * Allocates all device memory up front.  Positions must be set next
+ * (vmc_init_positions or vmc_set_positions). */
+vmc_status vmc_create(const vmc_system* systems, int n_walkers, const vmc_solver_params* params,
+                      void* stream, vmc_ctx** out);
+vmc_status vmc_destroy(vmc_ctx* ctx);
+
+/* Start walker w at r_i = wrap(Z_i + jitter N(0,1)^3) with normals from
+ * Philox4x32-10(key = seeds[w], counter = (0, i, 0, j)), for every walker; then build
+ * the Slater matrices, reorder (Sec. 3.1) and factor (Sec. 3.2).  seeds: host,
+ * n_walkers entries. */
+vmc_status vmc_init_positions(vmc_ctx* ctx, const uint64_t* seeds, double jitter);
+/* Set walker w's positions (host, n*3 doubles, particle order) and rebuild its matrix,
+ * ordering and factorisation. */
+vmc_status vmc_set_positions(vmc_ctx* ctx, int walker, const double* xyz);
+vmc_status vmc_get_positions(vmc_ctx* ctx, int walker, double* xyz);
+int vmc_walker_n(const vmc_ctx* ctx, int walker);
+
+/* Single move: det(A')/det(A) for moving particle k of walker w to r_new (host, 3
+ * doubles; wrapped into the box).  Nothing is committed; the solve is kept so that
+ * vmc_accept can commit it.  Sec. 3 Eq. 13. */
+vmc_status vmc_ratio(vmc_ctx* ctx, int walker, int k, const double r_new[3], double* ratio);
+/* Commit the move of the last vmc_ratio on walker w: replace the Slater row and
+ * apply the rank-one preconditioner update (Sec. 3.2 Eq. 17).  VMC_ERR_STATE if
+ * no ratio is pending. */
+vmc_status vmc_accept(vmc_ctx* ctx, int walker);
+
+/* Metropolis sweeps (Sec. 2.2): every walker moves particles 0..n-1 in order,
+ * r' = wrap(r + sigma N(0,1)^3) (counter (sweep, i, 1, j)), accepted iff
+ * ratio^2 > U with U from counter (sweep, i, 2, 0), key seeds[w].  Sweep indices
+ * continue from the context's sweep counter.  Logs (host, nullable): walker-major,
+ * sum_w n_sweeps * n_w entries, walker w's block starting at n_sweeps * (n_0 + ... + n_{w-1}). */
+vmc_status vmc_sweep(vmc_ctx* ctx, int n_sweeps, double sigma, const uint64_t* seeds,
+                     uint8_t* accept_log, double* ratio_log);
+/* Same, with device-resident logs (nullable) and no host synchronisation: the call
+ * only enqueues work on the context's stream. */
+vmc_status vmc_sweep_async(vmc_ctx* ctx, int n_sweeps, double sigma, const uint64_t* seeds_dev,
+                           uint8_t* accept_log_dev, double* ratio_log_dev);
+/* Device status check after vmc_sweep_async: synchronises and returns the first
+ * walker error. */
+vmc_status vmc_synchronize(vmc_ctx* ctx);
+
+vmc_status vmc_get_stats(vmc_ctx* ctx, int walker, vmc_stats* out);
+vmc_status vmc_reset_stats(vmc_ctx* ctx);
+const char* vmc_last_error(const vmc_ctx* ctx);
+/* Sweeps done so far (the sweep counter used for the proposals). */
+int64_t vmc_sweep_count(const vmc_ctx* ctx);
+vmc_status vmc_set_sweep_count(vmc_ctx* ctx, int64_t sweeps);
+
+/* ---- inspection (tests) -------------------------------------------------------- */
+/* Walker w's reordered Slater matrix A_p = P A Q_0 as dense row-major n*n (host),
+ * and the permutations: part_of_row[r] = particle in row r, orb_of_col[c] = orbital
+ * in column c. Any pointer may be NULL. */
+vmc_status vmc_get_matrix(vmc_ctx* ctx, int walker, double* A_dense, int* part_of_row,
+                          int* orb_of_col);
+/* Walker w's ILUTP factors of A_p Q = L U as dense row-major n*n (host): L unit lower
+ * (diagonal stored as 1), U upper, perm[t] = column of A_p in factor column t. */
+vmc_status vmc_get_factors(vmc_ctx* ctx, int walker, double* L_dense, double* U_dense, int* perm);
+/* Apply the current preconditioner M (Sec. 3.2 Eq. 18) of walker w to v (host, n,
+ * indexed by rows of A_p) giving z (host, n, indexed by columns of A_p). */
+vmc_status vmc_apply_preconditioner(vmc_ctx* ctx, int walker, const double* v, double* z);
+/* Force a reorder + refactorisation of walker w now (tests). */
+vmc_status vmc_refactor(vmc_ctx* ctx, int walker, int reorder);
+/* Philox4x32-10 on the device for n counters (host arrays ctr: 4n words, key: 2
+ * words, out: 4n words): checks the device generator against its definition. */
+vmc_status vmc_philox_device(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,682 @@
+// vmc_capi.cu -- the C ABI (include/vmc.h): context, device memory, launches,
+// host-side geometry/layout, statistics and inspection.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/vmc.h"
+#include "vmc_internal.h"
+
+using namespace vmc;
+
+// ---------------------------------------------------------------------------
+// layout: sites (Sec. 2.1, Sec. 4), the fixed colour order of orbitals, and a
+// rigorous bound on the number of orbitals within r_c of any point.
+// ---------------------------------------------------------------------------
+namespace vmc {
+
+static int count_sites_within(int lattice, double a, double gx, double gy, double gz, double R) {
+  const int per = lattice == 1 ? 2 : 1;
+  int cnt = 0;
+  const int lo[3] = {(int)std::floor((gx - R) / a) - 1, (int)std::floor((gy - R) / a) - 1, (int)std::floor((gz - R) / a) - 1};
+  const int hi[3] = {(int)std::floor((gx + R) / a) + 1, (int)std::floor((gy + R) / a) + 1, (int)std::floor((gz + R) / a) + 1};
+  for (int z = lo[2]; z <= hi[2]; ++z)
+    for (int y = lo[1]; y <= hi[1]; ++y)
+      for (int x = lo[0]; x <= hi[0]; ++x)
+        for (int b = 0; b < per; ++b) {
+          const double off = 0.5 * b;
+          const double dx = gx - a * (x + off), dy = gy - a * (y + off), dz = gz - a * (z + off);
+          if (dx * dx + dy * dy + dz * dz <= R * R) ++cnt;
+        }
+  return cnt;
+}
+
+int make_layout(int K, int lattice, double a, double r_c, Layout& out, const char** why) {
+  if (K < 2 || K > 64) { *why = "K must be in [2, 64]"; return 1; }
+  if (lattice != 0 && lattice != 1) { *why = "lattice must be 0 (sc) or 1 (bcc)"; return 1; }
+  if (!(a > 0.0) || !(r_c > 0.0)) { *why = "a and r_c must be positive"; return 1; }
+  const double L = K * a;
+  if (!(r_c < 0.5 * L)) { *why = "r_c must be below half the box side"; return 1; }
+  const double cover = lattice == 1 ? a * std::sqrt(5.0) / 4.0 : a * std::sqrt(3.0) / 2.0;
+  if (!(r_c > cover)) { *why = "r_c must exceed the lattice covering radius (else A can be singular)"; return 1; }
+  const int per = lattice == 1 ? 2 : 1;
+  const int n = K * K * K * per;
+  out.n = n;
+  out.per = per;
+  out.Z.assign((size_t)n * 3, 0.0);
+  for (int jz = 0; jz < K; ++jz)
+    for (int jy = 0; jy < K; ++jy)
+      for (int jx = 0; jx < K; ++jx)
+        for (int b = 0; b < per; ++b) {
+          const int j = (jx + K * (jy + K * jz)) * per + b;
+          const double off = 0.5 * (double)b;
+          out.Z[3 * j + 0] = a * ((double)jx + off);
+          out.Z[3 * j + 1] = a * ((double)jy + off);
+          out.Z[3 * j + 2] = a * ((double)jz + off);
+        }
+  // colour of orbital j: (x mod 3, y mod 3, z mod 3, basis); same-colour sites are >= 3a
+  // apart (except across the periodic seam when 3 does not divide K)
+  std::vector<std::pair<int, int>> key(n);
+  for (int j = 0; j < n; ++j) {
+    const int cell = j / per, b = j % per;
+    const int cx = cell % K, cy = (cell / K) % K, cz = cell / (K * K);
+    key[j] = {(cx % 3) + 3 * (cy % 3) + 9 * (cz % 3) + 27 * b, j};
+  }
+  std::sort(key.begin(), key.end());
+  out.orb_of_col.assign(n, 0);
+  out.col_of_orb.assign(n, 0);
+  for (int c = 0; c < n; ++c) {
+    out.orb_of_col[c] = key[c].second;
+    out.col_of_orb[key[c].second] = c;
+  }
+  // Row capacity: every point lies within h sqrt(3)/2 of a grid point g (spacing h),
+  // so count(point, r_c) <= count(g, r_c + h sqrt(3)/2); the lattice has period a.
+  const int G = 16;
+  const double h = a / G, R = r_c + h * std::sqrt(3.0) / 2.0;
+  int mx = 0;
+  for (int z = 0; z <= G; ++z)
+    for (int y = 0; y <= G; ++y)
+      for (int x = 0; x <= G; ++x) mx = std::max(mx, count_sites_within(lattice, a, x * h, y * h, z * h, R));
+  out.cap = std::min(n, (mx + 3) / 4 * 4);
+  if (out.cap > kMaxRow) { *why = "r_c too large: a Slater row could exceed 256 orbitals"; return 1; }
+  return 0;
+}
+
+}  // namespace vmc
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct vmc_ctx {
+  int nw = 0;
+  std::vector<vmc_system> sys;
+  vmc_solver_params prm{};
+  Params P{};
+  cudaStream_t stream = nullptr;
+  int threads = 256;
+  bool fp64 = false;
+  std::vector<Walker> hw;
+  Walker* dW = nullptr;
+  Ctl* dCtl = nullptr;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  int64_t sweeps = 0;
+  std::string err;
+  long long total_n = 0;
+  int max_n = 0;
+  uint64_t* d_seeds = nullptr;
+  uint8_t* d_acc = nullptr;
+  double* d_ratio = nullptr;
+  size_t log_cap = 0;
+  std::vector<char> pending;
+  bool ready = false;
+};
+
+static vmc_status fail(vmc_ctx* c, vmc_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+static vmc_status cuda_fail(vmc_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? VMC_ERR_OOM : VMC_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(call, what)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
+static LaunchCfg cfg(const vmc_ctx* c) { return LaunchCfg{c->stream, c->threads, c->fp64}; }
+
+extern "C" vmc_status vmc_default_params(vmc_solver_params* p) {
+  if (!p) return VMC_ERR_INVALID;
+  p->drop_tol = 1e-4;
+  p->permtol = 0.5;
+  p->lfil_extra = -1;
+  p->gmres_m = 30;
+  p->max_restarts = 10;
+  p->inner_rtol = 0.0;
+  p->ratio_tol = 1e-12;
+  p->N_max = 100.0;
+  p->slow_factor = 4.0;
+  p->max_updates = 32;
+  p->precision = VMC_PREC_MIXED;
+  p->engine = VMC_ENGINE_PERSISTENT;
+  p->block_threads = 0;
+  p->sm_refresh = 1;
+  return VMC_OK;
+}
+
+namespace {
+struct Carve {
+  size_t off = 0;
+  template <typename T>
+  size_t take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    const size_t o = off;
+    off += count * sizeof(T);
+    return o;
+  }
+};
+}  // namespace
+
+extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const vmc_solver_params* params,
+                                 void* stream, vmc_ctx** out) {
+  if (!out) return VMC_ERR_INVALID;
+  *out = nullptr;
+  if (!systems || n_walkers <= 0 || n_walkers > 65535) return VMC_ERR_INVALID;
+  vmc_ctx* ctx = new vmc_ctx();
+  ctx->nw = n_walkers;
+  ctx->sys.assign(systems, systems + n_walkers);
+  if (params) ctx->prm = *params; else vmc_default_params(&ctx->prm);
+  vmc_solver_params& p = ctx->prm;
+  ctx->stream = (cudaStream_t)stream;
+  auto bad = [&](const std::string& m) { ctx->err = m; return VMC_ERR_INVALID; };
+  vmc_status st = VMC_OK;
+  if (p.gmres_m < 1 || p.gmres_m > kMaxM) st = bad("gmres_m must be in [1, 40]");
+  else if (p.max_updates < 0 || p.max_updates > kMaxUpd) st = bad("max_updates must be in [0, 128]");
+  else if (p.precision != VMC_PREC_FP64 && p.precision != VMC_PREC_MIXED) st = bad("precision");
+  else if (p.engine < VMC_ENGINE_PLAIN || p.engine > VMC_ENGINE_PERSISTENT) st = bad("engine (dense SM has its own entry)");
+  else if (p.block_threads != 0 && (p.block_threads < 64 || p.block_threads > kMaxThreads || p.block_threads % 32))
+    st = bad("block_threads must be 0 or a multiple of 32 in [64, 512]");
+  else if (!(p.drop_tol >= 0.0) || !(p.permtol >= 0.0) || p.max_restarts < 0) st = bad("ILUTP/GMRES parameters");
+  if (st != VMC_OK) { *out = ctx; return st; }
+  ctx->fp64 = p.precision == VMC_PREC_FP64;
+  ctx->threads = p.block_threads ? p.block_threads : 256;
+  ctx->P.drop_tol = p.drop_tol;
+  ctx->P.permtol = p.permtol;
+  ctx->P.lfil_extra = p.lfil_extra;
+  ctx->P.m = p.gmres_m;
+  ctx->P.max_restarts = p.max_restarts;
+  ctx->P.max_updates = p.max_updates;
+  ctx->P.inner_rtol = p.inner_rtol > 0.0 ? p.inner_rtol : (ctx->fp64 ? 1e-10 : 1e-5);
+  ctx->P.ratio_tol = p.ratio_tol > 0.0 ? p.ratio_tol : 1e-12;
+  ctx->P.N_max = p.N_max;
+  ctx->P.slow_factor = p.slow_factor;
+
+  // layouts (one per distinct system)
+  std::vector<Layout> lay(n_walkers);
+  for (int w = 0; w < n_walkers; ++w) {
+    const vmc_system& s = systems[w];
+    bool reused = false;
+    for (int v = 0; v < w && !reused; ++v)
+      if (!std::memcmp(&systems[v], &s, sizeof(vmc_system))) { lay[w] = lay[v]; reused = true; }
+    if (reused) continue;
+    const char* why = "";
+    if (make_layout(s.K, s.lattice, s.a, s.r_c, lay[w], &why) || !(s.kappa > 0.0)) {
+      ctx->err = std::string("walker ") + std::to_string(w) + ": " + (s.kappa > 0.0 ? why : "kappa must be positive");
+      *out = ctx;
+      return VMC_ERR_INVALID;
+    }
+  }
+  // carve one arena
+  const size_t Tsz = ctx->fp64 ? sizeof(double) : sizeof(float);
+  const int m = p.gmres_m, mu = std::max(1, p.max_updates);
+  std::vector<std::vector<size_t>> offs(n_walkers);
+  Carve cv;
+  ctx->hw.resize(n_walkers);
+  long long base = 0;
+  for (int w = 0; w < n_walkers; ++w) {
+    const Layout& L = lay[w];
+    const int n = L.n, cap = L.cap;
+    const int pmax = p.lfil_extra >= 0 ? p.lfil_extra : (cap + 1) / 2;
+    const int capLU = cap + pmax + 2;
+    auto& o = offs[w];
+    o.push_back(cv.take<double>((size_t)n * 3));       // 0 Z
+    o.push_back(cv.take<int>(n));                      // 1 col_of_orb
+    o.push_back(cv.take<int>(n));                      // 2 orb_of_col
+    o.push_back(cv.take<double>((size_t)n * 3));       // 3 R
+    o.push_back(cv.take<int>(n));                      // 4 row_of_part
+    o.push_back(cv.take<int>(n));                      // 5 part_of_row
+    o.push_back(cv.take<int>((size_t)n * cap));        // 6 a_col
+    o.push_back(cv.take<double>((size_t)n * cap));     // 7 a_val
+    o.push_back(cv.take<float>((size_t)n * cap));      // 8 a_val32
+    o.push_back(cv.take<int>(n));                      // 9 a_len
+    o.push_back(cv.take<int>((size_t)n * capLU));      // 10 l_col
+    o.push_back(cv.take<double>((size_t)n * capLU));   // 11 l_val64
+    o.push_back(cv.take<float>(ctx->fp64 ? 0 : (size_t)n * capLU));  // 12 l_valT (fp32)
+    o.push_back(cv.take<int>(n));                      // 13 l_len
+    o.push_back(cv.take<int>((size_t)n * capLU));      // 14 u_col
+    o.push_back(cv.take<double>((size_t)n * capLU));   // 15 u_val64
+    o.push_back(cv.take<float>(ctx->fp64 ? 0 : (size_t)n * capLU));  // 16 u_valT
+    o.push_back(cv.take<int>(n));                      // 17 u_len
+    o.push_back(cv.take<double>(n));                   // 18 u_dinv64
+    o.push_back(cv.take<float>(ctx->fp64 ? 0 : n));    // 19 u_dinvT
+    o.push_back(cv.take<int>(n));                      // 20 perm
+    o.push_back(cv.take<int>(n));                      // 21 iperm
+    o.push_back(cv.take<int>(n));                      // 22 lev_l
+    o.push_back(cv.take<int>(n));                      // 23 lev_u
+    o.push_back(cv.take<int>(n + 1));                  // 24 l_lvl_ptr
+    o.push_back(cv.take<int>(n));                      // 25 l_lvl_rows
+    o.push_back(cv.take<int>(n + 1));                  // 26 u_lvl_ptr
+    o.push_back(cv.take<int>(n));                      // 27 u_lvl_rows
+    o.push_back(cv.take<int>(n + 1));                  // 28 lvl_cur
+    o.push_back(cv.take<double>(n));                   // 29 wrow
+    o.push_back(cv.take<int>(n));                      // 30 wpos
+    o.push_back(cv.take<int>(n));                      // 31 gP
+    o.push_back(cv.take<int>(n));                      // 32 gQ
+    o.push_back(cv.take<char>((size_t)mu * n * Tsz)); // 33 upd_z
+    o.push_back(cv.take<int>((size_t)mu * kMaxU));     // 34 upd_ucol
+    o.push_back(cv.take<char>((size_t)mu * kMaxU * Tsz));  // 35 upd_uval
+    o.push_back(cv.take<int>(mu));                     // 36 upd_ulen
+    o.push_back(cv.take<double>((size_t)kMaxUpd * kMaxUpd));  // 37 upd_G
+    o.push_back(cv.take<char>((size_t)(m + 1) * n * Tsz));    // 38 V
+    o.push_back(cv.take<char>((size_t)m * n * Tsz));          // 39 Zk
+    o.push_back(cv.take<char>((size_t)n * Tsz));              // 40 tv
+    o.push_back(cv.take<double>(n));                   // 41 x64
+    o.push_back(cv.take<double>(n));                   // 42 r64
+    o.push_back(cv.take<int>(cap));                    // 43 pend_acol
+    o.push_back(cv.take<double>(cap));                 // 44 pend_aval
+    o.push_back(cv.take<int>(kMaxU));                  // 45 pend_ucol
+    o.push_back(cv.take<double>(kMaxU));               // 46 pend_uval
+    Walker& W = ctx->hw[w];
+    std::memset(&W, 0, sizeof(W));
+    W.n = n; W.K = systems[w].K; W.lattice = systems[w].lattice; W.cap = cap; W.capLU = capLU;
+    W.m = m; W.mu = mu; W.per = L.per;
+    W.a = systems[w].a; W.kappa = systems[w].kappa; W.rc = systems[w].r_c;
+    W.rc2 = systems[w].r_c * systems[w].r_c; W.L = systems[w].K * systems[w].a;
+    W.log_base = base;
+    base += n;
+    ctx->max_n = std::max(ctx->max_n, n);
+  }
+  ctx->total_n = base;
+  const size_t ctl_off = cv.take<Ctl>(n_walkers);
+  const size_t walk_off = cv.take<Walker>(n_walkers);
+  ctx->arena_bytes = cv.off + 256;
+  cudaError_t e = cudaMalloc((void**)&ctx->arena, ctx->arena_bytes);
+  if (e != cudaSuccess) { *out = ctx; return cuda_fail(ctx, e, "cudaMalloc arena"); }
+  e = cudaMemsetAsync(ctx->arena, 0, ctx->arena_bytes, ctx->stream);
+  if (e != cudaSuccess) { *out = ctx; return cuda_fail(ctx, e, "cudaMemset arena"); }
+  char* A = ctx->arena;
+  ctx->dCtl = (Ctl*)(A + ctl_off);
+  ctx->dW = (Walker*)(A + walk_off);
+  for (int w = 0; w < n_walkers; ++w) {
+    const auto& o = offs[w];
+    Walker& W = ctx->hw[w];
+    W.Z = (const double*)(A + o[0]);
+    W.col_of_orb = (const int*)(A + o[1]);
+    W.orb_of_col = (const int*)(A + o[2]);
+    W.R = (double*)(A + o[3]);
+    W.row_of_part = (int*)(A + o[4]);
+    W.part_of_row = (int*)(A + o[5]);
+    W.a_col = (int*)(A + o[6]);
+    W.a_val = (double*)(A + o[7]);
+    W.a_val32 = (float*)(A + o[8]);
+    W.a_len = (int*)(A + o[9]);
+    W.l_col = (int*)(A + o[10]);
+    W.l_val64 = (double*)(A + o[11]);
+    W.l_valT = ctx->fp64 ? (void*)W.l_val64 : (void*)(A + o[12]);
+    W.l_len = (int*)(A + o[13]);
+    W.u_col = (int*)(A + o[14]);
+    W.u_val64 = (double*)(A + o[15]);
+    W.u_valT = ctx->fp64 ? (void*)W.u_val64 : (void*)(A + o[16]);
+    W.u_len = (int*)(A + o[17]);
+    W.u_dinv64 = (double*)(A + o[18]);
+    W.u_dinvT = ctx->fp64 ? (void*)W.u_dinv64 : (void*)(A + o[19]);
+    W.perm = (int*)(A + o[20]);
+    W.iperm = (int*)(A + o[21]);
+    W.lev_l = (int*)(A + o[22]);
+    W.lev_u = (int*)(A + o[23]);
+    W.l_lvl_ptr = (int*)(A + o[24]);
+    W.l_lvl_rows = (int*)(A + o[25]);
+    W.u_lvl_ptr = (int*)(A + o[26]);
+    W.u_lvl_rows = (int*)(A + o[27]);
+    W.lvl_cur = (int*)(A + o[28]);
+    W.wrow = (double*)(A + o[29]);
+    W.wpos = (int*)(A + o[30]);
+    W.gP = (int*)(A + o[31]);
+    W.gQ = (int*)(A + o[32]);
+    W.upd_z = (void*)(A + o[33]);
+    W.upd_ucol = (int*)(A + o[34]);
+    W.upd_uval = (void*)(A + o[35]);
+    W.upd_ulen = (int*)(A + o[36]);
+    W.upd_G = (double*)(A + o[37]);
+    W.V = (void*)(A + o[38]);
+    W.Zk = (void*)(A + o[39]);
+    W.tv = (void*)(A + o[40]);
+    W.x64 = (double*)(A + o[41]);
+    W.r64 = (double*)(A + o[42]);
+    W.pend_acol = (int*)(A + o[43]);
+    W.pend_aval = (double*)(A + o[44]);
+    W.pend_ucol = (int*)(A + o[45]);
+    W.pend_uval = (double*)(A + o[46]);
+    W.ctl = ctx->dCtl + w;
+    const Layout& L = lay[w];
+    e = cudaMemcpyAsync((void*)W.Z, L.Z.data(), sizeof(double) * L.Z.size(), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((void*)W.col_of_orb, L.col_of_orb.data(), sizeof(int) * L.n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((void*)W.orb_of_col, L.orb_of_col.data(), sizeof(int) * L.n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) { *out = ctx; return cuda_fail(ctx, e, "upload layout"); }
+  }
+  e = cudaMemcpyAsync(ctx->dW, ctx->hw.data(), sizeof(Walker) * n_walkers, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_seeds, sizeof(uint64_t) * n_walkers);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) { *out = ctx; return cuda_fail(ctx, e, "upload walkers"); }
+  ctx->pending.assign(n_walkers, 0);
+  *out = ctx;
+  return VMC_OK;
+}
+
+extern "C" vmc_status vmc_destroy(vmc_ctx* ctx) {
+  if (!ctx) return VMC_ERR_INVALID;
+  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->d_seeds) cudaFree(ctx->d_seeds);
+  if (ctx->d_acc) cudaFree(ctx->d_acc);
+  if (ctx->d_ratio) cudaFree(ctx->d_ratio);
+  delete ctx;
+  return VMC_OK;
+}
+
+extern "C" const char* vmc_last_error(const vmc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+extern "C" int vmc_walker_n(const vmc_ctx* ctx, int walker) {
+  if (!ctx || walker < 0 || walker >= ctx->nw) return -1;
+  return ctx->hw[walker].n;
+}
+extern "C" int64_t vmc_sweep_count(const vmc_ctx* ctx) { return ctx ? ctx->sweeps : -1; }
+extern "C" vmc_status vmc_set_sweep_count(vmc_ctx* ctx, int64_t sweeps) {
+  if (!ctx || sweeps < 0) return VMC_ERR_INVALID;
+  ctx->sweeps = sweeps;
+  return VMC_OK;
+}
+
+static vmc_status check_walker_status(vmc_ctx* ctx) {
+  std::vector<Ctl> h(ctx->nw);
+  CK(cudaMemcpyAsync(h.data(), ctx->dCtl, sizeof(Ctl) * ctx->nw, cudaMemcpyDeviceToHost, ctx->stream), "read status");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  for (int w = 0; w < ctx->nw; ++w)
+    if (h[w].status != ST_OK)
+      return fail(ctx, (vmc_status)h[w].status, "walker " + std::to_string(w) + " failed with status " + std::to_string(h[w].status));
+  return VMC_OK;
+}
+
+static vmc_status setup_all(vmc_ctx* ctx, int w0, int nwalk) {
+  CK(launch_setup(cfg(ctx), ctx->dW, w0, nwalk, ctx->P), "setup kernel");
+  for (int w = w0; w < w0 + nwalk; ++w) ctx->pending[w] = 0;
+  ctx->ready = true;
+  return check_walker_status(ctx);
+}
+
+extern "C" vmc_status vmc_init_positions(vmc_ctx* ctx, const uint64_t* seeds, double jitter) {
+  if (!ctx || !seeds || !(jitter >= 0.0)) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  CK(cudaMemcpyAsync(ctx->d_seeds, seeds, sizeof(uint64_t) * ctx->nw, cudaMemcpyHostToDevice, ctx->stream), "seeds");
+  CK(cudaMemsetAsync(ctx->dCtl, 0, sizeof(Ctl) * ctx->nw, ctx->stream), "reset walkers");
+  CK(launch_init_positions(cfg(ctx), ctx->dW, ctx->nw, ctx->d_seeds, jitter), "init positions");
+  return setup_all(ctx, 0, ctx->nw);
+}
+
+extern "C" vmc_status vmc_set_positions(vmc_ctx* ctx, int walker, const double* xyz) {
+  if (!ctx || !xyz || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  const Walker& W = ctx->hw[walker];
+  std::vector<double> r(xyz, xyz + (size_t)W.n * 3);
+  for (double& v : r) {
+    if (!std::isfinite(v)) return fail(ctx, VMC_ERR_INVALID, "non-finite position");
+    double y = v - W.L * std::floor(v / W.L);
+    if (y >= W.L) y -= W.L;
+    v = y;
+  }
+  CK(cudaMemcpyAsync(W.R, r.data(), sizeof(double) * r.size(), cudaMemcpyHostToDevice, ctx->stream), "positions");
+  CK(cudaMemsetAsync(ctx->dCtl + walker, 0, sizeof(Ctl), ctx->stream), "reset walker");
+  return setup_all(ctx, walker, 1);
+}
+
+extern "C" vmc_status vmc_get_positions(vmc_ctx* ctx, int walker, double* xyz) {
+  if (!ctx || !xyz || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  const Walker& W = ctx->hw[walker];
+  CK(cudaMemcpyAsync(xyz, W.R, sizeof(double) * 3 * W.n, cudaMemcpyDeviceToHost, ctx->stream), "positions");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  return VMC_OK;
+}
+
+extern "C" vmc_status vmc_ratio(vmc_ctx* ctx, int walker, int k, const double r_new[3], double* ratio) {
+  if (!ctx || !r_new || !ratio || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  if (!ctx->ready) return fail(ctx, VMC_ERR_STATE, "positions not set");
+  const Walker& W = ctx->hw[walker];
+  if (k < 0 || k >= W.n) return fail(ctx, VMC_ERR_INVALID, "particle index out of range");
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(r_new[d])) return fail(ctx, VMC_ERR_INVALID, "non-finite position");
+  CK(launch_ratio(cfg(ctx), ctx->dW, walker, ctx->P, k, r_new), "ratio kernel");
+  Ctl h;
+  CK(cudaMemcpyAsync(&h, ctx->dCtl + walker, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream), "read ratio");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  if (h.status != ST_OK) return fail(ctx, (vmc_status)h.status, "walker failed with status " + std::to_string(h.status));
+  if (!h.pend_valid) { ctx->pending[walker] = 0; return fail(ctx, VMC_ERR_NOCONV, "solve did not converge"); }
+  *ratio = h.pend_ratio;
+  ctx->pending[walker] = 1;
+  return VMC_OK;
+}
+
+extern "C" vmc_status vmc_accept(vmc_ctx* ctx, int walker) {
+  if (!ctx || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  if (!ctx->pending[walker]) return fail(ctx, VMC_ERR_STATE, "vmc_accept without a pending vmc_ratio");
+  CK(launch_accept(cfg(ctx), ctx->dW, walker, ctx->P), "accept kernel");
+  ctx->pending[walker] = 0;
+  return check_walker_status(ctx);
+}
+
+static vmc_status ensure_logs(vmc_ctx* ctx, size_t entries) {
+  if (entries <= ctx->log_cap) return VMC_OK;
+  if (ctx->d_acc) cudaFree(ctx->d_acc);
+  if (ctx->d_ratio) cudaFree(ctx->d_ratio);
+  ctx->d_acc = nullptr;
+  ctx->d_ratio = nullptr;
+  ctx->log_cap = 0;
+  CK(cudaMalloc((void**)&ctx->d_acc, entries), "log alloc");
+  CK(cudaMalloc((void**)&ctx->d_ratio, entries * sizeof(double)), "log alloc");
+  ctx->log_cap = entries;
+  return VMC_OK;
+}
+
+static vmc_status enqueue_sweeps(vmc_ctx* ctx, int n_sweeps, double sigma, const uint64_t* d_seeds, uint8_t* acc,
+                                 double* ratio) {
+  const LaunchCfg L = cfg(ctx);
+  const long long s0 = ctx->sweeps;
+  const int eng = ctx->prm.engine;
+  if (eng == VMC_ENGINE_PERSISTENT) {
+    CK(launch_sweep(L, ctx->dW, 0, ctx->nw, ctx->P, n_sweeps, s0, sigma, d_seeds, acc, ratio), "sweep kernel");
+  } else if (eng == VMC_ENGINE_STEP) {
+    for (int s = 0; s < n_sweeps; ++s)
+      for (int q = 0; q < ctx->max_n; ++q)
+        CK(launch_step(L, ctx->dW, 0, ctx->nw, ctx->P, q, n_sweeps, s, s0, sigma, d_seeds, acc, ratio), "step kernel");
+  } else {  // PLAIN: one walker per launch, one launch per move step
+    for (int s = 0; s < n_sweeps; ++s)
+      for (int w = 0; w < ctx->nw; ++w)
+        for (int q = 0; q < ctx->hw[w].n; ++q)
+          CK(launch_step(L, ctx->dW, w, 1, ctx->P, q, n_sweeps, s, s0, sigma, d_seeds, acc, ratio), "step kernel");
+  }
+  ctx->sweeps += n_sweeps;
+  return VMC_OK;
+}
+
+extern "C" vmc_status vmc_sweep(vmc_ctx* ctx, int n_sweeps, double sigma, const uint64_t* seeds, uint8_t* accept_log,
+                                double* ratio_log) {
+  if (!ctx || !seeds || n_sweeps < 0 || !(sigma >= 0.0)) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  if (!ctx->ready) return fail(ctx, VMC_ERR_STATE, "positions not set");
+  if (n_sweeps == 0) return VMC_OK;
+  const size_t entries = (size_t)n_sweeps * ctx->total_n;
+  vmc_status st = VMC_OK;
+  if (accept_log || ratio_log) {
+    st = ensure_logs(ctx, entries);
+    if (st != VMC_OK) return st;
+  }
+  CK(cudaMemcpyAsync(ctx->d_seeds, seeds, sizeof(uint64_t) * ctx->nw, cudaMemcpyHostToDevice, ctx->stream), "seeds");
+  st = enqueue_sweeps(ctx, n_sweeps, sigma, ctx->d_seeds, accept_log ? ctx->d_acc : nullptr,
+                      ratio_log ? ctx->d_ratio : nullptr);
+  if (st != VMC_OK) return st;
+  for (int w = 0; w < ctx->nw; ++w) ctx->pending[w] = 0;
+  if (accept_log) CK(cudaMemcpyAsync(accept_log, ctx->d_acc, entries, cudaMemcpyDeviceToHost, ctx->stream), "accept log");
+  if (ratio_log)
+    CK(cudaMemcpyAsync(ratio_log, ctx->d_ratio, entries * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "ratio log");
+  return check_walker_status(ctx);
+}
+
+extern "C" vmc_status vmc_sweep_async(vmc_ctx* ctx, int n_sweeps, double sigma, const uint64_t* seeds_dev,
+                                      uint8_t* accept_log_dev, double* ratio_log_dev) {
+  if (!ctx || !seeds_dev || n_sweeps < 0 || !(sigma >= 0.0)) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  if (!ctx->ready) return fail(ctx, VMC_ERR_STATE, "positions not set");
+  if (n_sweeps == 0) return VMC_OK;
+  for (int w = 0; w < ctx->nw; ++w) ctx->pending[w] = 0;
+  return enqueue_sweeps(ctx, n_sweeps, sigma, seeds_dev, accept_log_dev, ratio_log_dev);
+}
+
+extern "C" vmc_status vmc_synchronize(vmc_ctx* ctx) {
+  if (!ctx) return VMC_ERR_INVALID;
+  return check_walker_status(ctx);
+}
+
+extern "C" vmc_status vmc_get_stats(vmc_ctx* ctx, int walker, vmc_stats* out) {
+  if (!ctx || !out || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  Ctl h;
+  CK(cudaMemcpyAsync(&h, ctx->dCtl + walker, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream), "stats");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  std::memset(out, 0, sizeof(*out));
+  out->proposals = h.proposals;
+  out->accepts = h.accepts;
+  out->solves = h.solves;
+  out->inner_iterations = h.inner_its;
+  out->first_pass_iterations = h.first_its;
+  out->outer_passes = h.outer_passes;
+  out->reorders = h.reorders;
+  out->reorder_monitor = h.reorder_monitor;
+  out->reorder_noconv = h.reorder_noconv;
+  out->reorder_slow = h.reorder_slow;
+  out->reorder_breakdown = h.reorder_breakdown;
+  out->refactors_updates = h.refactors_updates;
+  out->factorizations = h.factorizations;
+  out->pivots = h.last_pivots;
+  out->N_max_seen = h.N_max_seen;
+  out->N_sum = h.N_sum;
+  out->nnz_A = h.nnz_A;
+  out->nnz_LU = h.nnz_LU;
+  out->levels_L = h.nlev_l;
+  out->levels_U = h.nlev_u;
+  out->n_updates = h.n_upd;
+  out->status = h.status;
+  for (int b = 0; b < kHistBins; ++b) out->its_hist[b] = h.hist[b];
+  return VMC_OK;
+}
+
+extern "C" vmc_status vmc_reset_stats(vmc_ctx* ctx) {
+  if (!ctx) return VMC_ERR_INVALID;
+  std::vector<Ctl> h(ctx->nw);
+  CK(cudaMemcpyAsync(h.data(), ctx->dCtl, sizeof(Ctl) * ctx->nw, cudaMemcpyDeviceToHost, ctx->stream), "stats");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  for (Ctl& c : h) {
+    c.proposals = c.accepts = c.solves = c.inner_its = c.first_its = c.outer_passes = 0;
+    c.reorders = c.reorder_monitor = c.reorder_noconv = c.reorder_slow = c.reorder_breakdown = 0;
+    c.refactors_updates = c.factorizations = 0;
+    c.N_max_seen = c.N_sum = 0.0;
+    for (long long& b : c.hist) b = 0;
+  }
+  CK(cudaMemcpyAsync(ctx->dCtl, h.data(), sizeof(Ctl) * ctx->nw, cudaMemcpyHostToDevice, ctx->stream), "stats");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  return VMC_OK;
+}
+
+// ---- inspection ------------------------------------------------------------------
+template <typename T>
+static cudaError_t d2h(T* dst, const T* src, size_t count, cudaStream_t s) {
+  return cudaMemcpyAsync(dst, src, sizeof(T) * count, cudaMemcpyDeviceToHost, s);
+}
+
+extern "C" vmc_status vmc_get_matrix(vmc_ctx* ctx, int walker, double* A_dense, int* part_of_row, int* orb_of_col) {
+  if (!ctx || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  const Walker& W = ctx->hw[walker];
+  const int n = W.n, cap = W.cap;
+  std::vector<int> col((size_t)n * cap), len(n), por(n), ooc(n);
+  std::vector<double> val((size_t)n * cap);
+  CK(d2h(col.data(), W.a_col, col.size(), ctx->stream), "matrix");
+  CK(d2h(val.data(), W.a_val, val.size(), ctx->stream), "matrix");
+  CK(d2h(len.data(), W.a_len, len.size(), ctx->stream), "matrix");
+  CK(d2h(por.data(), W.part_of_row, por.size(), ctx->stream), "matrix");
+  CK(d2h(ooc.data(), W.orb_of_col, ooc.size(), ctx->stream), "matrix");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  if (A_dense) {
+    std::fill(A_dense, A_dense + (size_t)n * n, 0.0);
+    for (int r = 0; r < n; ++r) {
+      const int p = por[r];
+      for (int t = 0; t < len[p]; ++t) A_dense[(size_t)r * n + col[(size_t)p * cap + t]] = val[(size_t)p * cap + t];
+    }
+  }
+  if (part_of_row) std::copy(por.begin(), por.end(), part_of_row);
+  if (orb_of_col) std::copy(ooc.begin(), ooc.end(), orb_of_col);
+  return VMC_OK;
+}
+
+extern "C" vmc_status vmc_get_factors(vmc_ctx* ctx, int walker, double* L_dense, double* U_dense, int* perm) {
+  if (!ctx || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  const Walker& W = ctx->hw[walker];
+  const int n = W.n, c = W.capLU;
+  std::vector<int> lc((size_t)n * c), ll(n), uc((size_t)n * c), ul(n), pm(n);
+  std::vector<double> lv((size_t)n * c), uv((size_t)n * c), dv(n);
+  CK(d2h(lc.data(), W.l_col, lc.size(), ctx->stream), "factors");
+  CK(d2h(lv.data(), W.l_val64, lv.size(), ctx->stream), "factors");
+  CK(d2h(ll.data(), W.l_len, ll.size(), ctx->stream), "factors");
+  CK(d2h(uc.data(), W.u_col, uc.size(), ctx->stream), "factors");
+  CK(d2h(uv.data(), W.u_val64, uv.size(), ctx->stream), "factors");
+  CK(d2h(ul.data(), W.u_len, ul.size(), ctx->stream), "factors");
+  CK(d2h(dv.data(), W.u_dinv64, dv.size(), ctx->stream), "factors");
+  CK(d2h(pm.data(), W.perm, pm.size(), ctx->stream), "factors");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  if (L_dense) {
+    std::fill(L_dense, L_dense + (size_t)n * n, 0.0);
+    for (int r = 0; r < n; ++r) {
+      L_dense[(size_t)r * n + r] = 1.0;
+      for (int t = 0; t < ll[r]; ++t) L_dense[(size_t)r * n + lc[(size_t)r * c + t]] = lv[(size_t)r * c + t];
+    }
+  }
+  if (U_dense) {
+    std::fill(U_dense, U_dense + (size_t)n * n, 0.0);
+    for (int r = 0; r < n; ++r) {
+      U_dense[(size_t)r * n + r] = 1.0 / dv[r];
+      for (int t = 0; t < ul[r]; ++t) U_dense[(size_t)r * n + uc[(size_t)r * c + t]] = uv[(size_t)r * c + t];
+    }
+  }
+  if (perm) std::copy(pm.begin(), pm.end(), perm);
+  return VMC_OK;
+}
+
+extern "C" vmc_status vmc_apply_preconditioner(vmc_ctx* ctx, int walker, const double* v, double* z) {
+  if (!ctx || !v || !z || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  if (!ctx->ready) return fail(ctx, VMC_ERR_STATE, "positions not set");
+  const Walker& W = ctx->hw[walker];
+  CK(cudaMemcpyAsync(W.r64, v, sizeof(double) * W.n, cudaMemcpyHostToDevice, ctx->stream), "vector");
+  CK(launch_apply_precond(cfg(ctx), ctx->dW, walker), "precond kernel");
+  CK(cudaMemcpyAsync(z, W.x64, sizeof(double) * W.n, cudaMemcpyDeviceToHost, ctx->stream), "vector");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  ctx->pending[walker] = 0;
+  return VMC_OK;
+}
+
+extern "C" vmc_status vmc_refactor(vmc_ctx* ctx, int walker, int reorder) {
+  if (!ctx || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  if (!ctx->ready) return fail(ctx, VMC_ERR_STATE, "positions not set");
+  CK(launch_refactor(cfg(ctx), ctx->dW, walker, ctx->P, reorder), "refactor kernel");
+  ctx->pending[walker] = 0;
+  return check_walker_status(ctx);
+}
+
+extern "C" vmc_status vmc_philox_device(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n) {
+  if (!ctr || !key || !out || n <= 0) return VMC_ERR_INVALID;
+  uint32_t *dc = nullptr, *dk = nullptr, *dout = nullptr;
+  vmc_status st = VMC_OK;
+  if (cudaMalloc((void**)&dc, sizeof(uint32_t) * 4 * n) != cudaSuccess ||
+      cudaMalloc((void**)&dk, sizeof(uint32_t) * 2) != cudaSuccess ||
+      cudaMalloc((void**)&dout, sizeof(uint32_t) * 4 * n) != cudaSuccess) {
+    st = VMC_ERR_OOM;
+  } else if (cudaMemcpy(dc, ctr, sizeof(uint32_t) * 4 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(dk, key, sizeof(uint32_t) * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+             launch_philox(dc, dk, dout, n, 0) != cudaSuccess ||
+             cudaMemcpy(out, dout, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    st = VMC_ERR_CUDA;
+  }
+  if (dc) cudaFree(dc);
+  if (dk) cudaFree(dk);
+  if (dout) cudaFree(dout);
+  return st;
+}

@@ -1,0 +1,396 @@
+// vmc_engine.cu -- kernels of the sparse determinant-ratio engine and their launchers.
+//
+// Every kernel runs one CTA per walker.  A Metropolis step (Sec. 2.2) is:
+//   propose r' (Philox, purpose 1) -> Slater row a' and u = a' - a_k (Sec. 3 Eq. 12)
+//   -> solve A_p x = e_r by preconditioned GMRES (Sec. 3.2 Eq. 15) with FP64 refinement
+//   -> controller: reorder + refactor when N > N_max, GMRES fails to converge in m
+//      iterations, or the iterations reach slow_factor x the running average (Sec. 4)
+//   -> ratio 1 + u^T x (Sec. 3 Eq. 13), accept iff ratio^2 > U (Sec. 2.2)
+//   -> on accept: replace the row and push (z_hat = x / ratio, u) onto the update
+//      chain (Sec. 3.2 Eq. 17); a new ILUTP once the chain holds max_updates entries
+//      (Sec. 3.2, last paragraph).
+#include "vmc_internal.h"
+#include "vmc_krylov.cuh"
+
+namespace vmc {
+
+// ---------------------------------------------------------------------------
+// device: solve + controller for the move in shared memory (sh.acol/aval, sh.ucol/uval)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __noinline__ void solve_with_controller(const Walker& w, const Params& P, int k, SolveOut& o, Shared& sh) {
+  Ctl* c = w.ctl;
+  const double rtol = P.inner_rtol;
+  int brow = w.row_of_part[k];
+  solve_first<T>(w, P, brow, rtol, o, sh);
+  int cause = 0;
+  const long long cnt = c->its_cnt;
+  const double avg = cnt > 0 ? c->its_sum / (double)cnt : 0.0;
+  if (!o.conv1) cause = 2;
+  else if (o.N > P.N_max) cause = 1;
+  else if (cnt >= 10 && (double)o.its1 >= P.slow_factor * avg) cause = 3;
+  __syncthreads();
+  if (cause) {
+    int fl = factor_block<T>(w, P, sh, true);
+    if (threadIdx.x == 0) {
+      c->reorders += 1;
+      if (cause == 1) c->reorder_monitor += 1;
+      if (cause == 2) c->reorder_noconv += 1;
+      if (cause == 3) c->reorder_slow += 1;
+      if (fl & 2) c->status = ST_CAPACITY;
+    }
+    __syncthreads();
+    brow = w.row_of_part[k];
+    const int its_before = o.its1;
+    solve_first<T>(w, P, brow, rtol, o, sh);
+    o.total_its += its_before;
+  } else if (threadIdx.x == 0) {
+    c->its_sum += (double)o.its1;
+    c->its_cnt += 1;
+  }
+  const double floor_rtol = rtol;
+  refine<T>(w, P, brow, floor_rtol, 2 + P.max_restarts, o, sh);
+  if (threadIdx.x == 0) {
+    c->solves += cause ? 2 : 1;
+    c->inner_its += o.total_its;
+    c->first_its += o.its1;
+    c->outer_passes += o.passes;
+    c->N_max_seen = fmax(c->N_max_seen, o.N);
+    c->N_sum += o.N;
+    c->hist[min(o.its1, kHistBins - 1)] += 1;
+    if (o.status != ST_OK && c->status == ST_OK) c->status = o.status;
+  }
+  __syncthreads();
+}
+
+// Commit the move in shared memory for particle k (row replace + preconditioner update).
+template <typename T>
+__device__ __noinline__ void commit_move(const Walker& w, const Params& P, int k, double ratio, Shared& sh) {
+  const int tid = threadIdx.x, nt = blockDim.x, n = w.n, cap = w.cap;
+  const int alen = sh.alen, ulen = sh.ulen;
+  for (int t = tid; t < alen; t += nt) {
+    w.a_col[(size_t)k * cap + t] = sh.acol[t];
+    w.a_val[(size_t)k * cap + t] = sh.aval[t];
+    w.a_val32[(size_t)k * cap + t] = (float)sh.aval[t];
+  }
+  if (tid == 0) {
+    w.a_len[k] = alen;
+    w.R[3 * k] = sh.rnew[0];
+    w.R[3 * k + 1] = sh.rnew[1];
+    w.R[3 * k + 2] = sh.rnew[2];
+  }
+  Ctl* c = w.ctl;
+  const int s = c->n_upd;
+  __syncthreads();
+  if (s < P.max_updates) {
+    T* Zh = (T*)w.upd_z;
+    T* Uv = (T*)w.upd_uval;
+    const double inv = 1.0 / ratio;
+    for (int i = tid; i < n; i += nt) Zh[(size_t)s * n + i] = (T)(w.x64[i] * inv);
+    for (int t = tid; t < ulen; t += nt) {
+      w.upd_ucol[(size_t)s * kMaxU + t] = sh.ucol[t];
+      Uv[(size_t)s * kMaxU + t] = (T)sh.uval[t];
+    }
+    if (tid == 0) w.upd_ulen[s] = ulen;
+    __syncthreads();
+    // G[s][t] = u_s^T z_hat_t for t < s, from the stored (working-precision) values
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    for (int t = wid; t < s; t += nw) {
+      double acc = 0.0;
+      for (int e = lane; e < ulen; e += 32)
+        acc += (double)Uv[(size_t)s * kMaxU + e] * (double)Zh[(size_t)t * n + w.upd_ucol[(size_t)s * kMaxU + e]];
+      acc = warp_sum(acc);
+      if (lane == 0) w.upd_G[(size_t)s * kMaxUpd + t] = acc;
+    }
+    __syncthreads();
+    if (tid == 0) c->n_upd = s + 1;
+  } else {
+    int fl = factor_block<T>(w, P, sh, false);
+    if (tid == 0) c->refactors_updates += 1;
+    if (fl & 1) {
+      fl = factor_block<T>(w, P, sh, true);
+      if (tid == 0) { c->reorders += 1; c->reorder_breakdown += 1; }
+    }
+    if (tid == 0 && (fl & 2)) c->status = ST_CAPACITY;
+  }
+  __syncthreads();
+}
+
+// Build a' for the particle k at sh.rnew and u = a' - a_k (warp 0).  Returns false on
+// a capacity overflow (status set).
+__device__ __noinline__ bool build_move(const Walker& w, int k, Shared& sh) {
+  if (threadIdx.x < 32) {
+    const int alen = build_row_warp(w, sh.rnew, sh.acol, sh.aval, w.cap);
+    int ulen = 0;
+    if (alen >= 0) ulen = build_u_warp(w, k, sh.acol, sh.aval, alen, sh.ucol, sh.uval);
+    if (threadIdx.x == 0) { sh.alen = alen; sh.ulen = ulen; }
+  }
+  __syncthreads();
+  if (sh.alen < 0) {
+    if (threadIdx.x == 0) w.ctl->status = ST_CAPACITY;
+    __syncthreads();
+    return false;
+  }
+  return true;
+}
+
+// One Metropolis step of particle k (Sec. 2.2).
+template <typename T>
+__device__ __noinline__ void mc_step(const Walker& w, const Params& P, int k, uint64_t seed, uint32_t sweep, double sigma,
+                        uint8_t* acc_log, double* ratio_log, Shared& sh) {
+  Ctl* c = w.ctl;
+  const int st = c->status;
+  __syncthreads();
+  if (st != ST_OK) {
+    if (threadIdx.x == 0) {
+      if (acc_log) *acc_log = 0;
+      if (ratio_log) *ratio_log = 0.0;
+    }
+    return;
+  }
+  if (threadIdx.x == 0) {
+    double z[3];
+    normal3(seed, sweep, (uint32_t)k, 1u, z);
+    for (int d = 0; d < 3; ++d) sh.rnew[d] = wrap_box(__dadd_rn(w.R[3 * k + d], __dmul_rn(sigma, z[d])), w.L);
+  }
+  __syncthreads();
+  if (!build_move(w, k, sh)) return;
+  SolveOut o;
+  solve_with_controller<T>(w, P, k, o, sh);
+  const double U = accept_uniform(seed, sweep, (uint32_t)k);
+  const bool ok = o.status == ST_OK;
+  const bool acc = ok && __dmul_rn(o.ratio, o.ratio) > U;
+  if (threadIdx.x == 0) {
+    if (acc_log) *acc_log = acc ? 1 : 0;
+    if (ratio_log) *ratio_log = o.ratio;
+    c->proposals += 1;
+    c->accepts += acc ? 1 : 0;
+  }
+  if (acc) commit_move<T>(w, P, k, o.ratio, sh);
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) k_sweep(const Walker* __restrict__ W, int walker0, Params P, int n_sweeps,
+                                                long long sweep0, double sigma, const uint64_t* __restrict__ seeds,
+                                                uint8_t* acc_log, double* ratio_log) {
+  __shared__ Shared sh;
+  const int wi = walker0 + blockIdx.x;
+  const Walker& w = W[wi];
+  const uint64_t seed = seeds[wi];
+  const int n = w.n;
+  for (int s = 0; s < n_sweeps; ++s)
+    for (int k = 0; k < n; ++k) {
+      const long long idx = (long long)n_sweeps * w.log_base + (long long)s * n + k;
+      mc_step<T>(w, P, k, seed, (uint32_t)(sweep0 + s), sigma, acc_log ? acc_log + idx : nullptr,
+                 ratio_log ? ratio_log + idx : nullptr, sh);
+    }
+}
+
+// One step (particle q of sweep s_local of a batch of n_sweeps) for every walker in the grid.
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) k_step(const Walker* __restrict__ W, int walker0, Params P, int q, int n_sweeps,
+                                               int s_local, long long sweep0, double sigma,
+                                               const uint64_t* __restrict__ seeds, uint8_t* acc_log, double* ratio_log) {
+  __shared__ Shared sh;
+  const int wi = walker0 + blockIdx.x;
+  const Walker& w = W[wi];
+  if (q >= w.n) return;
+  const long long idx = (long long)n_sweeps * w.log_base + (long long)s_local * w.n + q;
+  mc_step<T>(w, P, q, seeds[wi], (uint32_t)(sweep0 + s_local), sigma, acc_log ? acc_log + idx : nullptr,
+             ratio_log ? ratio_log + idx : nullptr, sh);
+}
+
+// Single-move API: ratio for particle k moved to r_new (no commit); result in ctl.
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) k_ratio(const Walker* __restrict__ W, int wi, Params P, int k, double rx,
+                                                double ry, double rz) {
+  __shared__ Shared sh;
+  const Walker& w = W[wi];
+  Ctl* c = w.ctl;
+  if (threadIdx.x == 0) {
+    sh.rnew[0] = wrap_box(rx, w.L);
+    sh.rnew[1] = wrap_box(ry, w.L);
+    sh.rnew[2] = wrap_box(rz, w.L);
+    c->pend_valid = 0;
+  }
+  __syncthreads();
+  if (!build_move(w, k, sh)) return;
+  SolveOut o;
+  solve_with_controller<T>(w, P, k, o, sh);
+  for (int t = threadIdx.x; t < sh.alen; t += blockDim.x) { w.pend_acol[t] = sh.acol[t]; w.pend_aval[t] = sh.aval[t]; }
+  for (int t = threadIdx.x; t < sh.ulen; t += blockDim.x) { w.pend_ucol[t] = sh.ucol[t]; w.pend_uval[t] = sh.uval[t]; }
+  if (threadIdx.x == 0) {
+    c->pend_alen = sh.alen;
+    c->pend_ulen = sh.ulen;
+    c->pend_k = k;
+    c->pend_r[0] = sh.rnew[0]; c->pend_r[1] = sh.rnew[1]; c->pend_r[2] = sh.rnew[2];
+    c->pend_ratio = o.ratio;
+    c->pend_valid = o.status == ST_OK ? 1 : 0;
+    c->proposals += 1;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) k_accept(const Walker* __restrict__ W, int wi, Params P) {
+  __shared__ Shared sh;
+  const Walker& w = W[wi];
+  Ctl* c = w.ctl;
+  const int valid = c->pend_valid;
+  const int k = c->pend_k;
+  if (!valid) return;
+  if (threadIdx.x == 0) {
+    sh.alen = c->pend_alen; sh.ulen = c->pend_ulen;
+    sh.rnew[0] = c->pend_r[0]; sh.rnew[1] = c->pend_r[1]; sh.rnew[2] = c->pend_r[2];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < sh.alen; t += blockDim.x) { sh.acol[t] = w.pend_acol[t]; sh.aval[t] = w.pend_aval[t]; }
+  for (int t = threadIdx.x; t < sh.ulen; t += blockDim.x) { sh.ucol[t] = w.pend_ucol[t]; sh.uval[t] = w.pend_uval[t]; }
+  __syncthreads();
+  commit_move<T>(w, P, k, c->pend_ratio, sh);
+  if (threadIdx.x == 0) { c->pend_valid = 0; c->accepts += 1; }
+}
+
+// r = wrap(Z + jitter * N(0,1)^3), purpose 0, sweep 0.
+__global__ void k_init_positions(const Walker* __restrict__ W, const uint64_t* __restrict__ seeds, double jitter) {
+  const Walker& w = W[blockIdx.x];
+  const uint64_t seed = seeds[blockIdx.x];
+  for (int i = threadIdx.x; i < w.n; i += blockDim.x) {
+    double z[3];
+    normal3(seed, 0u, (uint32_t)i, 0u, z);
+    for (int d = 0; d < 3; ++d) w.R[3 * i + d] = wrap_box(__dadd_rn(w.Z[3 * i + d], __dmul_rn(jitter, z[d])), w.L);
+  }
+}
+
+// All Slater rows from the positions (warp per particle), then the initial pairing
+// (particle i with orbital i), the greedy reordering and the first factorisation.
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) k_setup(const Walker* __restrict__ W, int walker0, Params P) {
+  __shared__ Shared sh;
+  const Walker& w = W[walker0 + blockIdx.x];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  Ctl* c = w.ctl;
+  int bad = 0;
+  for (int p = wid; p < w.n; p += nw) {
+    const int len = build_row_warp(w, w.R + 3 * p, w.a_col + (size_t)p * w.cap, w.a_val + (size_t)p * w.cap, w.cap);
+    if (lane == 0) {
+      if (len < 0) bad = 1;
+      w.a_len[p] = len < 0 ? 0 : len;
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < w.n * w.cap; idx += blockDim.x) w.a_val32[idx] = (float)w.a_val[idx];
+  for (int col = threadIdx.x; col < w.n; col += blockDim.x) {
+    const int o = w.orb_of_col[col];
+    w.part_of_row[col] = o;
+    w.row_of_part[o] = col;
+  }
+  if (threadIdx.x == 0) {
+    c->n_upd = 0;
+    c->pend_valid = 0;
+    c->its_sum = 0.0;
+    c->its_cnt = 0;
+  }
+  __syncthreads();
+  const int fl = factor_block<T>(w, P, sh, true);
+  if (lane == 0 && bad) c->status = ST_CAPACITY;
+  if (threadIdx.x == 0 && (fl & 2)) c->status = ST_CAPACITY;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) k_refactor(const Walker* __restrict__ W, int wi, Params P, int reorder) {
+  __shared__ Shared sh;
+  const Walker& w = W[wi];
+  factor_block<T>(w, P, sh, reorder != 0);
+}
+
+// z = M v for the test entry point: v in r64 (FP64), result in x64 (FP64).
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) k_apply_precond(const Walker* __restrict__ W, int wi) {
+  __shared__ Shared sh;
+  const Walker& w = W[wi];
+  T* V = (T*)w.V;
+  T* Zk = (T*)w.Zk;
+  for (int i = threadIdx.x; i < w.n; i += blockDim.x) V[i] = (T)w.r64[i];
+  __syncthreads();
+  precond_apply<T>(w, V, Zk, sh);
+  for (int i = threadIdx.x; i < w.n; i += blockDim.x) w.x64[i] = (double)Zk[i];
+}
+
+__global__ void k_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t c[4] = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+  uint32_t k[2] = {key[0], key[1]};
+  uint32_t o[4];
+  philox4x32_10(c, k, o);
+  for (int j = 0; j < 4; ++j) out[4 * i + j] = o[j];
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+static cudaError_t launch_sweep_t(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P,
+                                  int n_sweeps, long long sweep0, double sigma, const uint64_t* seeds, uint8_t* acc,
+                                  double* ratio) {
+  k_sweep<T><<<nwalk, L.threads, 0, L.stream>>>(W, walker0, P, n_sweeps, sweep0, sigma, seeds, acc, ratio);
+  return cudaGetLastError();
+}
+template <typename T>
+static cudaError_t launch_step_t(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int q,
+                                 int n_sweeps, int s_local, long long sweep0, double sigma, const uint64_t* seeds,
+                                 uint8_t* acc, double* ratio) {
+  k_step<T><<<nwalk, L.threads, 0, L.stream>>>(W, walker0, P, q, n_sweeps, s_local, sweep0, sigma, seeds, acc, ratio);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int n_sweeps,
+                         long long sweep0, double sigma, const uint64_t* seeds, uint8_t* acc, double* ratio) {
+  return L.fp64 ? launch_sweep_t<double>(L, W, walker0, nwalk, P, n_sweeps, sweep0, sigma, seeds, acc, ratio)
+                : launch_sweep_t<float>(L, W, walker0, nwalk, P, n_sweeps, sweep0, sigma, seeds, acc, ratio);
+}
+cudaError_t launch_step(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int q,
+                        int n_sweeps, int s_local, long long sweep0, double sigma, const uint64_t* seeds,
+                        uint8_t* acc, double* ratio) {
+  return L.fp64 ? launch_step_t<double>(L, W, walker0, nwalk, P, q, n_sweeps, s_local, sweep0, sigma, seeds, acc, ratio)
+                : launch_step_t<float>(L, W, walker0, nwalk, P, q, n_sweeps, s_local, sweep0, sigma, seeds, acc, ratio);
+}
+cudaError_t launch_ratio(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int k, const double r[3]) {
+  if (L.fp64) k_ratio<double><<<1, L.threads, 0, L.stream>>>(W, wi, P, k, r[0], r[1], r[2]);
+  else k_ratio<float><<<1, L.threads, 0, L.stream>>>(W, wi, P, k, r[0], r[1], r[2]);
+  return cudaGetLastError();
+}
+cudaError_t launch_accept(const LaunchCfg& L, const Walker* W, int wi, const Params& P) {
+  if (L.fp64) k_accept<double><<<1, L.threads, 0, L.stream>>>(W, wi, P);
+  else k_accept<float><<<1, L.threads, 0, L.stream>>>(W, wi, P);
+  return cudaGetLastError();
+}
+cudaError_t launch_init_positions(const LaunchCfg& L, const Walker* W, int nwalk, const uint64_t* seeds, double jitter) {
+  k_init_positions<<<nwalk, 256, 0, L.stream>>>(W, seeds, jitter);
+  return cudaGetLastError();
+}
+cudaError_t launch_setup(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P) {
+  if (L.fp64) k_setup<double><<<nwalk, L.threads, 0, L.stream>>>(W, walker0, P);
+  else k_setup<float><<<nwalk, L.threads, 0, L.stream>>>(W, walker0, P);
+  return cudaGetLastError();
+}
+cudaError_t launch_refactor(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int reorder) {
+  if (L.fp64) k_refactor<double><<<1, L.threads, 0, L.stream>>>(W, wi, P, reorder);
+  else k_refactor<float><<<1, L.threads, 0, L.stream>>>(W, wi, P, reorder);
+  return cudaGetLastError();
+}
+cudaError_t launch_apply_precond(const LaunchCfg& L, const Walker* W, int wi) {
+  if (L.fp64) k_apply_precond<double><<<1, L.threads, 0, L.stream>>>(W, wi);
+  else k_apply_precond<float><<<1, L.threads, 0, L.stream>>>(W, wi);
+  return cudaGetLastError();
+}
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, cudaStream_t s) {
+  k_philox<<<(n + 127) / 128, 128, 0, s>>>(ctr, key, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace vmc

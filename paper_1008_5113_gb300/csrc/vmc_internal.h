@@ -1,0 +1,42 @@
+// vmc_internal.h -- declarations shared by the kernel translation unit and the C ABI
+// translation unit (host-side launchers and the layout helpers).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "vmc_device.cuh"
+
+namespace vmc {
+
+struct LaunchCfg {
+  cudaStream_t stream;
+  int threads;
+  bool fp64;
+};
+
+cudaError_t launch_sweep(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int n_sweeps,
+                         long long sweep0, double sigma, const uint64_t* seeds, uint8_t* acc, double* ratio);
+cudaError_t launch_step(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int q,
+                        int n_sweeps, int s_local, long long sweep0, double sigma, const uint64_t* seeds,
+                        uint8_t* acc, double* ratio);
+cudaError_t launch_ratio(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int k, const double r[3]);
+cudaError_t launch_accept(const LaunchCfg& L, const Walker* W, int wi, const Params& P);
+cudaError_t launch_init_positions(const LaunchCfg& L, const Walker* W, int nwalk, const uint64_t* seeds, double jitter);
+cudaError_t launch_setup(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P);
+cudaError_t launch_refactor(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int reorder);
+cudaError_t launch_apply_precond(const LaunchCfg& L, const Walker* W, int wi);
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, cudaStream_t s);
+
+// host-side geometry and layout (vmc_layout.cpp)
+struct Layout {
+  int n, per, cap;
+  std::vector<double> Z;       // n*3
+  std::vector<int> col_of_orb;  // n
+  std::vector<int> orb_of_col;  // n
+};
+// Returns 0, or a nonzero code with a message on invalid parameters.
+int make_layout(int K, int lattice, double a, double r_c, Layout& out, const char** why);
+
+}  // namespace vmc

@@ -1,0 +1,320 @@
+// vmc_krylov.cuh -- the per-move solve A_p z = e_r and the determinant ratio.
+//
+//   * M v = prod_s (I - z_hat_s u_s^T) Q (L U)^{-1} v                (Sec. 3.2 Eq. 18)
+//     forward/backward substitution level by level (rows of a level in parallel),
+//     then the column permutation Q, then the update chain fused into one pass:
+//     c_s = u_s^T w_0 - sum_{t<s} G[s][t] c_t,  w = w_0 - sum_s z_hat_s c_s.
+//   * right-preconditioned GMRES(m) on A_p M (Sec. 3.2 Eq. 15) with classical
+//     Gram-Schmidt applied twice, Givens rotations, and the effective stability
+//     N = max_j ||v_j - A_p M v_j||_2 over the Arnoldi vectors (Sec. 3.1 Eq. 10),
+//     computed in the same pass as the first projections.
+//   * FP64 iterative refinement: r = e_r - A_p x in FP64, inner GMRES in the working
+//     precision T on r, x += d; the ratio 1 + u^T x (Sec. 3 Eq. 13) in FP64.
+#pragma once
+#include "vmc_precond.cuh"
+
+namespace vmc {
+
+template <typename T>
+__device__ __forceinline__ const T* a_vals(const Walker& w);
+template <>
+__device__ __forceinline__ const float* a_vals<float>(const Walker& w) { return w.a_val32; }
+template <>
+__device__ __forceinline__ const double* a_vals<double>(const Walker& w) { return w.a_val; }
+
+// y = A_p x (thread per row; rows gathered through the particle slot of each row)
+template <typename T>
+__device__ __forceinline__ void spmv(const Walker& w, const T* __restrict__ x, T* __restrict__ y) {
+  const T* av = a_vals<T>(w);
+  const int n = w.n, cap = w.cap;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const int p = w.part_of_row[r];
+    const int len = w.a_len[p];
+    const int* c = w.a_col + (size_t)p * cap;
+    const T* v = av + (size_t)p * cap;
+    T acc = 0;
+    for (int t = 0; t < len; ++t) acc += v[t] * x[c[t]];
+    y[r] = acc;
+  }
+}
+
+// z = M v  (v indexed by rows, z by columns of A_p).  Block-wide, ends synchronised.
+template <typename T>
+__device__ __noinline__ void precond_apply(const Walker& w, const T* __restrict__ v, T* __restrict__ z, Shared& sh) {
+  const int n = w.n, tid = threadIdx.x, nt = blockDim.x, capLU = w.capLU;
+  T* y = (T*)w.tv;
+  const T* lv = (const T*)w.l_valT;
+  const T* uv = (const T*)w.u_valT;
+  const T* dv = (const T*)w.u_dinvT;
+  for (int i = tid; i < n; i += nt) y[i] = v[i];
+  __syncthreads();
+  const int nll = w.ctl->nlev_l, nlu = w.ctl->nlev_u;
+  for (int lev = 0; lev < nll; ++lev) {
+    const int b = w.l_lvl_ptr[lev], e = w.l_lvl_ptr[lev + 1];
+    for (int q = b + tid; q < e; q += nt) {
+      const int r = w.l_lvl_rows[q];
+      const int len = w.l_len[r];
+      const int* c = w.l_col + (size_t)r * capLU;
+      const T* vv = lv + (size_t)r * capLU;
+      T acc = y[r];
+      for (int t = 0; t < len; ++t) acc -= vv[t] * y[c[t]];
+      y[r] = acc;
+    }
+    __syncthreads();
+  }
+  for (int lev = 0; lev < nlu; ++lev) {
+    const int b = w.u_lvl_ptr[lev], e = w.u_lvl_ptr[lev + 1];
+    for (int q = b + tid; q < e; q += nt) {
+      const int r = w.u_lvl_rows[q];
+      const int len = w.u_len[r];
+      const int* c = w.u_col + (size_t)r * capLU;
+      const T* vv = uv + (size_t)r * capLU;
+      T acc = y[r];
+      for (int t = 0; t < len; ++t) acc -= vv[t] * y[c[t]];
+      y[r] = acc * dv[r];
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < n; t += nt) z[w.perm[t]] = y[t];
+  __syncthreads();
+  const int mu = w.ctl->n_upd;
+  if (mu > 0) {
+    const T* Zh = (const T*)w.upd_z;
+    const T* Uv = (const T*)w.upd_uval;
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    for (int s = wid; s < mu; s += nw) {       // d_s = u_s^T w_0 (sparse)
+      const int ul = w.upd_ulen[s];
+      const int* uc = w.upd_ucol + (size_t)s * kMaxU;
+      const T* uu = Uv + (size_t)s * kMaxU;
+      double acc = 0.0;
+      for (int t = lane; t < ul; t += 32) acc += (double)uu[t] * (double)z[uc[t]];
+      acc = warp_sum(acc);
+      if (lane == 0) sh.cupd[s] = acc;
+    }
+    __syncthreads();
+    if (tid == 0) {                             // c_s = d_s - sum_{t<s} G[s][t] c_t
+      const double* G = w.upd_G;
+      for (int s = 1; s < mu; ++s) {
+        double acc = sh.cupd[s];
+        for (int t = 0; t < s; ++t) acc -= G[(size_t)s * kMaxUpd + t] * sh.cupd[t];
+        sh.cupd[s] = acc;
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) {         // w = w_0 - sum_s z_hat_s c_s
+      T acc = z[i];
+      for (int s = 0; s < mu; ++s) acc -= Zh[(size_t)s * n + i] * (T)sh.cupd[s];
+      z[i] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// Dot products <V_k, wv> for k = 0..nk-1 into out[k]; if mon, also ||V_{nk-1} - wv||^2
+// into out[nk].  One warp per dot.  Ends synchronised.
+template <typename T>
+__device__ __forceinline__ void multi_dot(const T* __restrict__ V, int n, int nk, const T* __restrict__ wv,
+                                          double* out, bool mon) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int total = nk + (mon ? 1 : 0);
+  for (int k = wid; k < total; k += nw) {
+    T a0 = 0, a1 = 0;
+    if (k < nk) {
+      const T* vk = V + (size_t)k * n;
+      int i = lane;
+      for (; i + 32 < n; i += 64) { a0 += vk[i] * wv[i]; a1 += vk[i + 32] * wv[i + 32]; }
+      if (i < n) a0 += vk[i] * wv[i];
+    } else {
+      const T* vk = V + (size_t)(nk - 1) * n;
+      for (int i = lane; i < n; i += 32) { const T d = vk[i] - wv[i]; a0 += d * d; }
+    }
+    const double s = warp_sum((double)a0 + (double)a1);
+    if (lane == 0) out[k] = s;
+  }
+  __syncthreads();
+}
+
+// Right-preconditioned GMRES(m) on A_p M d = rhs (FP64 rhs, norm beta); adds the
+// correction M V y into x64.  Returns the iteration count; conv and the monitor N.
+template <typename T>
+__device__ __noinline__ int gmres_inner(const Walker& w, const Params& P, double beta, double rtol, bool& conv,
+                           double& Nmon, Shared& sh) {
+  const int n = w.n, tid = threadIdx.x, nt = blockDim.x, m = P.m;
+  T* V = (T*)w.V;
+  T* Zk = (T*)w.Zk;
+  const double inv = 1.0 / beta;
+  for (int i = tid; i < n; i += nt) V[i] = (T)(w.r64[i] * inv);
+  if (tid == 0) { sh.g[0] = beta; sh.iflag[1] = 0; }
+  double mon2 = 0.0;
+  __syncthreads();
+  int j = 0;
+  for (; j < m;) {
+    T* vj = V + (size_t)j * n;
+    T* zj = Zk + (size_t)j * n;
+    T* wv = V + (size_t)(j + 1) * n;
+    precond_apply<T>(w, vj, zj, sh);
+    spmv<T>(w, zj, wv);
+    __syncthreads();
+    multi_dot<T>(V, n, j + 1, wv, sh.h1, true);          // projections + monitor
+    mon2 = fmax(mon2, sh.h1[j + 1]);
+    for (int i = tid; i < n; i += nt) {
+      T acc = wv[i];
+      for (int k = 0; k <= j; ++k) acc -= (T)sh.h1[k] * V[(size_t)k * n + i];
+      wv[i] = acc;
+    }
+    __syncthreads();
+    multi_dot<T>(V, n, j + 1, wv, sh.h2, false);         // second Gram-Schmidt pass
+    T nrm_t = 0;
+    for (int i = tid; i < n; i += nt) {
+      T acc = wv[i];
+      for (int k = 0; k <= j; ++k) acc -= (T)sh.h2[k] * V[(size_t)k * n + i];
+      wv[i] = acc;
+      nrm_t += acc * acc;
+    }
+    const double nrm = sqrt(block_sum((double)nrm_t, sh));
+    const T sc = nrm > 0.0 ? (T)(1.0 / nrm) : (T)0;
+    for (int i = tid; i < n; i += nt) wv[i] *= sc;
+    if (tid == 0) {
+      double* H = sh.H;
+      for (int k = 0; k <= j; ++k) H[k * kMaxM + j] = sh.h1[k] + sh.h2[k];
+      H[(j + 1) * kMaxM + j] = nrm;
+      for (int k = 0; k < j; ++k) {
+        const double a0 = H[k * kMaxM + j], a1 = H[(k + 1) * kMaxM + j];
+        H[k * kMaxM + j] = sh.cs[k] * a0 + sh.sn[k] * a1;
+        H[(k + 1) * kMaxM + j] = -sh.sn[k] * a0 + sh.cs[k] * a1;
+      }
+      const double a0 = H[j * kMaxM + j], a1 = H[(j + 1) * kMaxM + j];
+      const double rr = sqrt(a0 * a0 + a1 * a1);
+      sh.cs[j] = rr == 0.0 ? 1.0 : a0 / rr;
+      sh.sn[j] = rr == 0.0 ? 0.0 : a1 / rr;
+      H[j * kMaxM + j] = rr;
+      H[(j + 1) * kMaxM + j] = 0.0;
+      sh.g[j + 1] = -sh.sn[j] * sh.g[j];
+      sh.g[j] = sh.cs[j] * sh.g[j];
+      sh.iflag[1] = (fabs(sh.g[j + 1]) <= rtol * beta) || nrm == 0.0;
+    }
+    __syncthreads();
+    ++j;
+    if (sh.iflag[1]) break;
+  }
+  conv = sh.iflag[1] != 0;
+  Nmon = sqrt(mon2);
+  if (tid == 0) {
+    const double* H = sh.H;
+    for (int k = j - 1; k >= 0; --k) {
+      double acc = sh.g[k];
+      for (int l = k + 1; l < j; ++l) acc -= H[k * kMaxM + l] * sh.y[l];
+      sh.y[k] = H[k * kMaxM + k] != 0.0 ? acc / H[k * kMaxM + k] : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) {
+    T acc = 0;
+    for (int k = 0; k < j; ++k) acc += (T)sh.y[k] * Zk[(size_t)k * n + i];
+    w.x64[i] += (double)acc;
+  }
+  __syncthreads();
+  return j;
+}
+
+// r64 = e_brow - A_p x64 (FP64); returns ||r64||_2 and, in *xnorm, ||x64||_2.
+// Ends synchronised.
+__device__ __forceinline__ double residual64(const Walker& w, int brow, double* xnorm, Shared& sh) {
+  const int n = w.n, cap = w.cap;
+  double ss = 0.0, xx = 0.0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const int p = w.part_of_row[r];
+    const int len = w.a_len[p];
+    const int* c = w.a_col + (size_t)p * cap;
+    const double* v = w.a_val + (size_t)p * cap;
+    double acc = 0.0;
+    for (int t = 0; t < len; ++t) acc = fma(v[t], w.x64[c[t]], acc);
+    const double rr = (r == brow ? 1.0 : 0.0) - acc;
+    w.r64[r] = rr;
+    ss += rr * rr;
+    const double xr = w.x64[r];
+    xx += xr * xr;
+  }
+  *xnorm = sqrt(block_sum(xx, sh));
+  return sqrt(block_sum(ss, sh));
+}
+
+// u^T x64 over the u list in shared memory (FP64).
+__device__ __forceinline__ double u_dot_x(const Walker& w, Shared& sh) {
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < sh.ulen; t += blockDim.x) acc += sh.uval[t] * w.x64[sh.ucol[t]];
+  return block_sum(acc, sh);
+}
+
+struct SolveOut {
+  double ratio;
+  int its1;
+  bool conv1;
+  double N;
+  int passes;
+  int total_its;
+  int status;
+};
+
+// First pass from x = 0 (used by the controller), then refinement passes until the
+// predicted ratio error |u^T d| ||r_j|| / ||r_{j-1}|| <= ratio_tol max(|ratio|, 1e-3).
+template <typename T>
+__device__ void solve_first(const Walker& w, const Params& P, int brow, double rtol, SolveOut& o, Shared& sh) {
+  const int n = w.n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    w.x64[i] = 0.0;
+    w.r64[i] = i == brow ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  bool conv = false;
+  double N = 0.0;
+  o.its1 = gmres_inner<T>(w, P, 1.0, rtol, conv, N, sh);
+  o.conv1 = conv;
+  o.N = N;
+  o.total_its = o.its1;
+  o.passes = 1;
+}
+
+// Refinement: the ratio error after a pass is u^T A^{-1} r.  It is predicted as the
+// larger of |u^T d_j| ||r_j|| / ||r_{j-1}|| (the last correction scaled by the last
+// residual reduction) and ||u|| ||x|| ||r_j|| (||x|| ~ ||A^{-1} e_r|| as a norm
+// estimate), and passes continue until it is <= ratio_tol max(|ratio|, 1e-3).  Each
+// pass asks the inner GMRES for only the reduction the goal needs (never below
+// rtol_floor).
+template <typename T>
+__device__ __noinline__ void refine(const Walker& w, const Params& P, int brow, double rtol_floor, int max_passes, SolveOut& o,
+                       Shared& sh) {
+  double usq = 0.0;
+  for (int t = threadIdx.x; t < sh.ulen; t += blockDim.x) usq += sh.uval[t] * sh.uval[t];
+  const double unorm = sqrt(block_sum(usq, sh));
+  double ratio_prev = 1.0;
+  double rprev = 1.0;
+  double ratio = 1.0 + u_dot_x(w, sh);
+  double xn = 0.0;
+  double rn = residual64(w, brow, &xn, sh);
+  o.status = ST_OK;
+  for (;;) {
+    const double delta = fabs(ratio - ratio_prev);
+    const double pred = fmax(delta * rn / rprev, unorm * xn * rn);
+    const double goal = P.ratio_tol * fmax(fabs(ratio), 1e-3);
+    if (pred <= goal || rn == 0.0) break;
+    if (o.passes >= max_passes) {
+      if (rn > 1e-6) o.status = ST_NOCONV;
+      break;
+    }
+    double need = 0.1 * goal / pred;
+    need = fmin(fmax(need, rtol_floor), 0.1);
+    bool conv = false;
+    double N = 0.0;
+    const int its = gmres_inner<T>(w, P, rn, need, conv, N, sh);
+    o.total_its += its;
+    o.passes += 1;
+    ratio_prev = ratio;
+    rprev = rn;
+    ratio = 1.0 + u_dot_x(w, sh);
+    rn = residual64(w, brow, &xn, sh);
+  }
+  o.ratio = ratio;
+}
+
+}  // namespace vmc

@@ -1,0 +1,269 @@
+"""ctypes binding of the C ABI in ``include/vmc.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+computation of its own: the work runs in ``libvmc.so``.  The library must have been
+built (``paper_1008_5113_gb300.build.build_library()`` or ``__graft_entry__.build()``);
+loading fails loudly otherwise -- there is no fallback path.
+
+Device buffers and streams may be passed as PyTorch CUDA tensors and
+``torch.cuda.Stream`` objects (their raw pointers/handles are forwarded).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from .build import LIB
+
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "VMC_OK", 1: "VMC_ERR_INVALID", 2: "VMC_ERR_CUDA", 3: "VMC_ERR_OOM", 4: "VMC_ERR_NOCONV",
+          5: "VMC_ERR_BREAKDOWN", 6: "VMC_ERR_TIMEOUT", 7: "VMC_ERR_STATE", 8: "VMC_ERR_CAPACITY"}
+PREC_FP64, PREC_MIXED = 0, 1
+ENGINE_PLAIN, ENGINE_STEP, ENGINE_PERSISTENT, ENGINE_DENSE_SM = 0, 1, 2, 3
+
+
+class VmcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class vmc_system(C.Structure):
+    _fields_ = [("K", C.c_int), ("lattice", C.c_int), ("a", C.c_double), ("kappa", C.c_double),
+                ("r_c", C.c_double)]
+
+
+class vmc_solver_params(C.Structure):
+    _fields_ = [("drop_tol", C.c_double), ("permtol", C.c_double), ("lfil_extra", C.c_int),
+                ("gmres_m", C.c_int), ("max_restarts", C.c_int), ("inner_rtol", C.c_double),
+                ("ratio_tol", C.c_double), ("N_max", C.c_double), ("slow_factor", C.c_double),
+                ("max_updates", C.c_int), ("precision", C.c_int), ("engine", C.c_int),
+                ("block_threads", C.c_int), ("sm_refresh", C.c_int)]
+
+
+class vmc_stats(C.Structure):
+    _fields_ = [("proposals", C.c_int64), ("accepts", C.c_int64), ("solves", C.c_int64),
+                ("inner_iterations", C.c_int64), ("first_pass_iterations", C.c_int64),
+                ("outer_passes", C.c_int64), ("reorders", C.c_int64), ("reorder_monitor", C.c_int64),
+                ("reorder_noconv", C.c_int64), ("reorder_slow", C.c_int64), ("reorder_breakdown", C.c_int64),
+                ("refactors_updates", C.c_int64), ("factorizations", C.c_int64), ("pivots", C.c_int64),
+                ("N_max_seen", C.c_double), ("N_sum", C.c_double), ("nnz_A", C.c_double), ("nnz_LU", C.c_double),
+                ("levels_L", C.c_int), ("levels_U", C.c_int), ("n_updates", C.c_int), ("status", C.c_int),
+                ("its_hist", C.c_int64 * 64)]
+
+
+# name -> (restype, argtypes); every symbol the header declares
+_SIG = {
+    "vmc_default_params": (C.c_int, [C.c_void_p]),
+    "vmc_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vmc_destroy": (C.c_int, [C.c_void_p]),
+    "vmc_init_positions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double]),
+    "vmc_set_positions": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "vmc_get_positions": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "vmc_walker_n": (C.c_int, [C.c_void_p, C.c_int]),
+    "vmc_ratio": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "vmc_accept": (C.c_int, [C.c_void_p, C.c_int]),
+    "vmc_sweep": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vmc_sweep_async": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vmc_synchronize": (C.c_int, [C.c_void_p]),
+    "vmc_get_stats": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "vmc_reset_stats": (C.c_int, [C.c_void_p]),
+    "vmc_last_error": (C.c_char_p, [C.c_void_p]),
+    "vmc_sweep_count": (C.c_int64, [C.c_void_p]),
+    "vmc_set_sweep_count": (C.c_int, [C.c_void_p, C.c_int64]),
+    "vmc_get_matrix": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vmc_get_factors": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vmc_apply_preconditioner": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "vmc_refactor": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "vmc_philox_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+}
+
+
+def lib():
+    """Load libvmc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise RuntimeError(f"{LIB} is not built; run __graft_entry__.build() (no CPU fallback exists)")
+            L = C.CDLL(LIB)
+            for name, (res, args) in _SIG.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _check(st: int, ctx=None):
+    if st != 0:
+        msg = lib().vmc_last_error(ctx).decode(errors="replace") if ctx is not None else ""
+        raise VmcError(st, msg)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def vmc_default_params() -> vmc_solver_params:
+    p = vmc_solver_params()
+    _check(lib().vmc_default_params(C.byref(p)))
+    return p
+
+
+def vmc_create(systems, params: vmc_solver_params | None = None, stream=None):
+    """systems: list of (K, lattice, a, kappa, r_c), one per walker. Returns the context."""
+    arr = (vmc_system * len(systems))(*[vmc_system(int(K), int(lat), float(a), float(k), float(rc))
+                                        for (K, lat, a, k, rc) in systems])
+    ctx = C.c_void_p()
+    st = lib().vmc_create(arr, len(systems), C.byref(params) if params is not None else None,
+                          _stream_handle(stream), C.byref(ctx))
+    if st != 0:
+        msg = lib().vmc_last_error(ctx).decode(errors="replace") if ctx.value else ""
+        if ctx.value:
+            lib().vmc_destroy(ctx)
+        raise VmcError(st, msg)
+    return ctx
+
+
+def vmc_destroy(ctx) -> None:
+    _check(lib().vmc_destroy(ctx))
+
+
+def vmc_init_positions(ctx, seeds, jitter: float) -> None:
+    s = np.ascontiguousarray(seeds, dtype=np.uint64)
+    _check(lib().vmc_init_positions(ctx, _p(s), float(jitter)), ctx)
+
+
+def vmc_walker_n(ctx, walker: int) -> int:
+    return lib().vmc_walker_n(ctx, walker)
+
+
+def vmc_set_positions(ctx, walker: int, xyz) -> None:
+    x = np.ascontiguousarray(xyz, dtype=np.float64)
+    _check(lib().vmc_set_positions(ctx, walker, _p(x)), ctx)
+
+
+def vmc_get_positions(ctx, walker: int) -> np.ndarray:
+    n = vmc_walker_n(ctx, walker)
+    x = np.zeros((n, 3))
+    _check(lib().vmc_get_positions(ctx, walker, _p(x)), ctx)
+    return x
+
+
+def vmc_ratio(ctx, walker: int, k: int, r_new) -> float:
+    r = np.ascontiguousarray(r_new, dtype=np.float64)
+    out = C.c_double(0.0)
+    _check(lib().vmc_ratio(ctx, walker, k, _p(r), C.byref(out)), ctx)
+    return out.value
+
+
+def vmc_accept(ctx, walker: int) -> None:
+    _check(lib().vmc_accept(ctx, walker), ctx)
+
+
+def vmc_sweep(ctx, n_sweeps: int, sigma: float, seeds, logs: bool = True):
+    """Host-log sweeps; returns (accept_log bool[], ratio_log float64[]) or (None, None)."""
+    s = np.ascontiguousarray(seeds, dtype=np.uint64)
+    total = sum(vmc_walker_n(ctx, w) for w in range(len(s))) * n_sweeps
+    acc = np.zeros(total, dtype=np.uint8) if logs else None
+    rat = np.zeros(total) if logs else None
+    _check(lib().vmc_sweep(ctx, n_sweeps, float(sigma), _p(s), _p(acc), _p(rat)), ctx)
+    return (acc.astype(bool), rat) if logs else (None, None)
+
+
+def vmc_sweep_async(ctx, n_sweeps: int, sigma: float, seeds_dev, accept_log_dev=None, ratio_log_dev=None) -> None:
+    _check(lib().vmc_sweep_async(ctx, n_sweeps, float(sigma), _p(seeds_dev), _p(accept_log_dev),
+                                 _p(ratio_log_dev)), ctx)
+
+
+def vmc_synchronize(ctx) -> None:
+    _check(lib().vmc_synchronize(ctx), ctx)
+
+
+def vmc_get_stats(ctx, walker: int) -> dict:
+    st = vmc_stats()
+    _check(lib().vmc_get_stats(ctx, walker, C.byref(st)), ctx)
+    d = {name: getattr(st, name) for name, _ in vmc_stats._fields_ if name != "its_hist"}
+    d["its_hist"] = list(st.its_hist)
+    return d
+
+
+def vmc_reset_stats(ctx) -> None:
+    _check(lib().vmc_reset_stats(ctx), ctx)
+
+
+def vmc_last_error(ctx) -> str:
+    return lib().vmc_last_error(ctx).decode(errors="replace")
+
+
+def vmc_sweep_count(ctx) -> int:
+    return lib().vmc_sweep_count(ctx)
+
+
+def vmc_set_sweep_count(ctx, sweeps: int) -> None:
+    _check(lib().vmc_set_sweep_count(ctx, sweeps), ctx)
+
+
+def vmc_get_matrix(ctx, walker: int):
+    n = vmc_walker_n(ctx, walker)
+    A = np.zeros((n, n))
+    por = np.zeros(n, dtype=np.int32)
+    ooc = np.zeros(n, dtype=np.int32)
+    _check(lib().vmc_get_matrix(ctx, walker, _p(A), _p(por), _p(ooc)), ctx)
+    return A, por, ooc
+
+
+def vmc_get_factors(ctx, walker: int):
+    n = vmc_walker_n(ctx, walker)
+    L = np.zeros((n, n))
+    U = np.zeros((n, n))
+    perm = np.zeros(n, dtype=np.int32)
+    _check(lib().vmc_get_factors(ctx, walker, _p(L), _p(U), _p(perm)), ctx)
+    return L, U, perm
+
+
+def vmc_apply_preconditioner(ctx, walker: int, v) -> np.ndarray:
+    vv = np.ascontiguousarray(v, dtype=np.float64)
+    z = np.zeros_like(vv)
+    _check(lib().vmc_apply_preconditioner(ctx, walker, _p(vv), _p(z)), ctx)
+    return z
+
+
+def vmc_refactor(ctx, walker: int, reorder: bool = True) -> None:
+    _check(lib().vmc_refactor(ctx, walker, 1 if reorder else 0), ctx)
+
+
+def vmc_philox_device(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros_like(c)
+    _check(lib().vmc_philox_device(_p(c), _p(k), _p(out), c.shape[0]))
+    return out
+
+
+def params(**kw) -> vmc_solver_params:
+    """vmc_default_params() with fields overridden by keyword."""
+    p = vmc_default_params()
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p

@@ -1,0 +1,74 @@
+"""CPU checks of the C ABI library: it loads, exports every entry point that
+include/vmc.h declares, and rejects invalid arguments without touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def vmc():
+    from paper_1008_5113_gb300.build import build_library
+
+    build_library()
+    from paper_1008_5113_gb300 import vmc as v
+
+    v.lib()
+    return v
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "vmc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vmc_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported_and_bound(vmc):
+    names = _declared()
+    assert len(names) >= 20
+    lib = vmc.lib()
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in vmc._SIG, f"binding lacks {name}"
+    assert set(vmc._SIG) == set(names)
+
+
+def test_default_params(vmc):
+    p = vmc.vmc_default_params()
+    assert p.drop_tol == 1e-4 and p.permtol == 0.5 and p.gmres_m == 30
+    assert p.N_max == 100.0 and p.slow_factor == 4.0 and p.lfil_extra == -1
+    assert p.precision == vmc.PREC_MIXED and p.engine == vmc.ENGINE_PERSISTENT
+
+
+@pytest.mark.parametrize("system,why", [
+    ((6, 0, 1.0, 2.0, 3.5), "half the box"),          # r_c >= L/2
+    ((6, 0, 1.0, 2.0, 0.8), "covering radius"),       # rows could be empty
+    ((1, 0, 1.0, 2.0, 0.9), "K must be"),
+    ((6, 2, 1.0, 2.0, 1.5), "lattice"),
+    ((6, 0, 1.0, -1.0, 1.5), "kappa"),
+    ((40, 0, 1.0, 0.5, 12.0), "256 orbitals"),
+])
+def test_create_rejects_invalid_systems(vmc, system, why):
+    with pytest.raises(vmc.VmcError) as e:
+        vmc.vmc_create([system])
+    assert e.value.status == 1 and why in str(e.value)
+
+
+@pytest.mark.parametrize("field,value", [("gmres_m", 0), ("gmres_m", 41), ("max_updates", 129),
+                                         ("block_threads", 100), ("block_threads", 1024), ("precision", 3),
+                                         ("engine", 7), ("drop_tol", -1.0)])
+def test_create_rejects_invalid_params(vmc, field, value):
+    with pytest.raises(vmc.VmcError) as e:
+        vmc.vmc_create([(6, 0, 1.0, 2.0, 1.5)], vmc.params(**{field: value}))
+    assert e.value.status == 1
+
+
+def test_null_arguments(vmc):
+    lib = vmc.lib()
+    assert lib.vmc_create(None, 1, None, None, None) == 1
+    assert lib.vmc_default_params(None) == 1
+    assert lib.vmc_destroy(None) == 1
+    assert lib.vmc_philox_device(None, None, None, 0) == 1

@@ -1,0 +1,141 @@
+"""GPU parity of the sparse determinant-ratio engine against the FP64 oracle.
+
+Bar: ratios within 1e-10 relative (1e-13 absolute where |ratio| < 1e-3) of the
+oracle's; Metropolis decisions identical except where |ratio^2 - U| < 1e-9 (after
+such a tie the two chains legitimately diverge and comparison stops there)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1008_5113_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+RTOL, ATOL, TIE = 1e-10, 1e-13, 1e-9
+
+
+@pytest.fixture(scope="module")
+def vmc():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_1008_5113_gb300.build import build_library
+
+    build_library()
+    O.build()
+    from paper_1008_5113_gb300 import vmc as v
+
+    return v
+
+
+def compare_chain(rat, acc, r_ref, a_ref, u_ref):
+    """Compare up to the first decision mismatch; returns the number compared."""
+    bad = np.nonzero(acc != a_ref)[0]
+    upto = int(bad[0]) if len(bad) else len(acc)
+    if upto < len(acc):
+        assert abs(r_ref[upto] ** 2 - u_ref[upto]) < TIE, f"decision differs at step {upto} away from a tie"
+    err = np.abs(rat[:upto] - r_ref[:upto])
+    lim = np.where(np.abs(r_ref[:upto]) >= 1e-3, RTOL * np.abs(r_ref[:upto]), ATOL)
+    worst = int(np.argmax(err - lim)) if upto else 0
+    assert np.all(err <= lim), f"ratio mismatch at step {worst}: {rat[worst]!r} vs {r_ref[worst]!r}"
+    return upto
+
+
+def test_device_philox_matches_definition(vmc):
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(257, 4), dtype=np.uint64).astype(np.uint32)
+    key = np.array([0xDEADBEEF, 0x01234567], dtype=np.uint32)
+    out = vmc.vmc_philox_device(ctr, key)
+    for i in range(0, 257, 16):
+        assert np.array_equal(out[i], O.philox4x32_10(ctr[i], key))
+    kat = vmc.vmc_philox_device(np.zeros((1, 4), np.uint32), np.zeros(2, np.uint32))
+    assert [int(x) for x in kat[0]] == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_initial_state_matches_oracle(vmc, prec):
+    K, seed = 6, 3
+    ctx = vmc.vmc_create([(K, 0, 1.0, 2.0, 1.5)], vmc.params(precision=0 if prec == "fp64" else 1))
+    try:
+        vmc.vmc_init_positions(ctx, [seed], 0.1)
+        R = vmc.vmc_get_positions(ctx, 0)
+        A, por, ooc = vmc.vmc_get_matrix(ctx, 0)
+        st = vmc.vmc_get_stats(ctx, 0)
+    finally:
+        vmc.vmc_destroy(ctx)
+    s = O.system(K)
+    R_ref = O.initial_positions(s, seed, 0.1)
+    assert np.abs(R - R_ref).max() < 1e-14
+    A_ref = O.slater_dense(s, O.sites(s), R_ref)
+    assert sorted(por) == list(range(216)) and sorted(ooc) == list(range(216))
+    A_orig = np.zeros_like(A)
+    A_orig[np.ix_(por, ooc)] = A
+    assert np.abs(A_orig - A_ref).max() < 1e-14
+    assert st["factorizations"] == 1 and st["status"] == 0
+    assert st["levels_L"] < 216 and st["levels_U"] < 216
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_plain_216_chain_matches_oracle(vmc, prec):
+    wl = WL.PLAIN_216
+    K = wl.Ks[0]
+    sweeps = 3
+    ctx = vmc.vmc_create(wl.systems(), vmc.params(precision=0 if prec == "fp64" else 1))
+    try:
+        vmc.vmc_init_positions(ctx, wl.seeds(), wl.jitter)
+        acc, rat = vmc.vmc_sweep(ctx, sweeps, wl.sigma, wl.seeds())
+        st = vmc.vmc_get_stats(ctx, 0)
+    finally:
+        vmc.vmc_destroy(ctx)
+    s = O.system(K, 0, wl.a, wl.kappa, wl.r_c)
+    R0 = O.initial_positions(s, 1, wl.jitter)
+    _, r_ref, a_ref, u_ref = O.chain(s, 1, wl.sigma, R0, sweeps, solver=O.SOLVER_DENSE_LU)
+    upto = compare_chain(rat, acc, r_ref, a_ref, u_ref)
+    assert upto > 300
+    assert st["proposals"] == sweeps * 216 and st["status"] == 0
+    assert 2 <= st["first_pass_iterations"] / st["solves"] <= 30
+
+
+def test_engines_agree_bitwise(vmc):
+    wl = WL.PLAIN_216
+    logs = {}
+    for eng in (vmc.ENGINE_PERSISTENT, vmc.ENGINE_STEP, vmc.ENGINE_PLAIN):
+        ctx = vmc.vmc_create(wl.systems() * 2, vmc.params(precision=0, engine=eng))
+        try:
+            vmc.vmc_init_positions(ctx, [1, 2], wl.jitter)
+            logs[eng] = vmc.vmc_sweep(ctx, 1, wl.sigma, [1, 2])
+        finally:
+            vmc.vmc_destroy(ctx)
+    a0, r0 = logs[vmc.ENGINE_PERSISTENT]
+    for eng in (vmc.ENGINE_STEP, vmc.ENGINE_PLAIN):
+        assert np.array_equal(logs[eng][0], a0)
+        assert np.array_equal(logs[eng][1], r0)
+
+
+def test_single_move_api_matches_oracle(vmc):
+    K, seed = 6, 5
+    s = O.system(K)
+    Z = O.sites(s)
+    R = O.initial_positions(s, seed, 0.1)
+    A = O.slater_dense(s, Z, R)
+    ctx = vmc.vmc_create([(K, 0, 1.0, 2.0, 1.5)], vmc.params(precision=1))
+    try:
+        vmc.vmc_set_positions(ctx, 0, R)
+        with pytest.raises(vmc.VmcError) as e:
+            vmc.vmc_accept(ctx, 0)
+        assert e.value.status == 7
+        for step, k in enumerate([0, 7, 100, 7, 215, 42]):
+            r_new = O.propose(s, 99, step, k, 0.3, R[k])
+            a_new = O.row_dense(s, Z, r_new)
+            ref, _ = O.ratio_dense(A, k, a_new)
+            got = vmc.vmc_ratio(ctx, 0, k, r_new)
+            assert abs(got - ref) <= RTOL * max(abs(ref), 1e-3)
+            if step % 2 == 0:
+                vmc.vmc_accept(ctx, 0)
+                A[k] = a_new
+                R[k] = r_new
+        assert np.abs(vmc.vmc_get_positions(ctx, 0) - R).max() == 0.0
+        # null move: ratio 1
+        assert abs(vmc.vmc_ratio(ctx, 0, 3, R[3]) - 1.0) < 1e-13
+    finally:
+        vmc.vmc_destroy(ctx)
