@@ -104,6 +104,15 @@ typedef struct {
   int n_updates;             /* current length of the update chain                         */
   int status;                /* vmc_status of this walker (sticky)                          */
   int64_t its_hist[64];      /* histogram of first-pass iterations (last bin: >= 63)       */
+  int64_t phase_cycles[16];  /* SM clock cycles by phase (thread 0 of the walker's CTA):
+                                0 row build, 1 first solve pass, 2 refinement passes,
+                                3 factorisation incl. reorder, 4 reordering, 5 commit + update,
+                                6 whole steps, 7 triangular solves, 8 update-chain apply,
+                                9 SpMV, 10 orthogonalisation + Givens, 11 FP64 residuals,
+                                12 ILUTP rows, 13 level sets + streams, 14 waits for
+                                triangular-factor chunks (inside 7), 15 unused */
+  double alg_bytes;          /* algorithmic (compulsory) bytes of the solves: per phase the
+                                matrix/factor values and indices, the vectors read and written */
 } vmc_stats;
 
 /* Fill p with the defaults above. */

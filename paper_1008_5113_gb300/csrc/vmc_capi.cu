@@ -105,6 +105,7 @@ struct vmc_ctx {
   Ctl* dCtl = nullptr;
   char* arena = nullptr;
   size_t arena_bytes = 0;
+  size_t smem = 0;
   int64_t sweeps = 0;
   std::string err;
   long long total_n = 0;
@@ -131,7 +132,7 @@ static vmc_status cuda_fail(vmc_ctx* c, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
   } while (0)
 
-static LaunchCfg cfg(const vmc_ctx* c) { return LaunchCfg{c->stream, c->threads, c->fp64}; }
+static LaunchCfg cfg(const vmc_ctx* c) { return LaunchCfg{c->stream, c->threads, c->fp64, c->smem}; }
 
 extern "C" vmc_status vmc_default_params(vmc_solver_params* p) {
   if (!p) return VMC_ERR_INVALID;
@@ -239,14 +240,15 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     o.push_back(cv.take<int>(n));                      // 9 a_len
     o.push_back(cv.take<int>((size_t)n * capLU));      // 10 l_col
     o.push_back(cv.take<double>((size_t)n * capLU));   // 11 l_val64
-    o.push_back(cv.take<float>(ctx->fp64 ? 0 : (size_t)n * capLU));  // 12 l_valT (fp32)
+    const size_t sbytes = (size_t)n * (192 + 12 * (size_t)capLU);
+    o.push_back(cv.take<unsigned char>(sbytes));       // 12 lstream
     o.push_back(cv.take<int>(n));                      // 13 l_len
     o.push_back(cv.take<int>((size_t)n * capLU));      // 14 u_col
     o.push_back(cv.take<double>((size_t)n * capLU));   // 15 u_val64
-    o.push_back(cv.take<float>(ctx->fp64 ? 0 : (size_t)n * capLU));  // 16 u_valT
+    o.push_back(cv.take<unsigned char>(sbytes));       // 16 ustream
     o.push_back(cv.take<int>(n));                      // 17 u_len
     o.push_back(cv.take<double>(n));                   // 18 u_dinv64
-    o.push_back(cv.take<float>(ctx->fp64 ? 0 : n));    // 19 u_dinvT
+    o.push_back(cv.take<int2>(2 * (size_t)n + 2));     // 19 lchunk | uchunk
     o.push_back(cv.take<int>(n));                      // 20 perm
     o.push_back(cv.take<int>(n));                      // 21 iperm
     o.push_back(cv.take<int>(n));                      // 22 lev_l
@@ -274,6 +276,8 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     o.push_back(cv.take<double>(cap));                 // 44 pend_aval
     o.push_back(cv.take<int>(kMaxU));                  // 45 pend_ucol
     o.push_back(cv.take<double>(kMaxU));               // 46 pend_uval
+    o.push_back(cv.take<int4>(n + 1));                 // 47 chunk_meta
+    o.push_back(cv.take<int>(n + 1));                  // 48 lvl_nchunk
     Walker& W = ctx->hw[w];
     std::memset(&W, 0, sizeof(W));
     W.n = n; W.K = systems[w].K; W.lattice = systems[w].lattice; W.cap = cap; W.capLU = capLU;
@@ -285,6 +289,37 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     ctx->max_n = std::max(ctx->max_n, n);
   }
   ctx->total_n = base;
+  {
+    // shared-memory plan: the triangular-solve vector in shared memory when it fits,
+    // and a ring of 2..8 chunk slots; aim for 2 CTAs per SM when walkers outnumber SMs
+    int dev = 0, optin = 0, per_sm = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int stat = kernel_static_smem(ctx->fp64);
+    if (optin <= 0 || per_sm <= 0 || nsm <= 0 || stat <= 0) {
+      *out = ctx;
+      return fail(ctx, VMC_ERR_CUDA, "no usable CUDA device (shared-memory attributes unavailable)");
+    }
+    const int ybytes = (int)(((size_t)ctx->max_n * Tsz + 127) / 128 * 128);
+    const int budget1 = optin - stat;
+    const int budget2 = per_sm / 2 - 1024 - stat;
+    int budget = budget1;
+    if (n_walkers > nsm && budget2 >= ybytes + 2 * kSlotBytes) budget = budget2;
+    if (ybytes + 2 * kSlotBytes <= budget) {
+      ctx->P.y_smem = 1;
+      ctx->P.y_bytes = ybytes;
+      ctx->P.ring_slots = std::min(kMaxSlots, (budget - ybytes) / kSlotBytes);
+    } else {
+      ctx->P.y_smem = 0;
+      ctx->P.y_bytes = 0;
+      ctx->P.ring_slots = std::min(kMaxSlots, budget / kSlotBytes);
+    }
+    // the rest of the budget is ILUTP scratch (work row, U-row cache)
+    ctx->smem = (size_t)std::max(budget, ctx->P.y_bytes + ctx->P.ring_slots * kSlotBytes);
+    ctx->P.dsm_bytes = (int)ctx->smem;
+  }
   const size_t ctl_off = cv.take<Ctl>(n_walkers);
   const size_t walk_off = cv.take<Walker>(n_walkers);
   ctx->arena_bytes = cv.off + 256;
@@ -310,14 +345,15 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     W.a_len = (int*)(A + o[9]);
     W.l_col = (int*)(A + o[10]);
     W.l_val64 = (double*)(A + o[11]);
-    W.l_valT = ctx->fp64 ? (void*)W.l_val64 : (void*)(A + o[12]);
+    W.lstream = (unsigned char*)(A + o[12]);
     W.l_len = (int*)(A + o[13]);
     W.u_col = (int*)(A + o[14]);
     W.u_val64 = (double*)(A + o[15]);
-    W.u_valT = ctx->fp64 ? (void*)W.u_val64 : (void*)(A + o[16]);
+    W.ustream = (unsigned char*)(A + o[16]);
     W.u_len = (int*)(A + o[17]);
     W.u_dinv64 = (double*)(A + o[18]);
-    W.u_dinvT = ctx->fp64 ? (void*)W.u_dinv64 : (void*)(A + o[19]);
+    W.lchunk = (int2*)(A + o[19]);
+    W.uchunk = W.lchunk + (W.n + 1);
     W.perm = (int*)(A + o[20]);
     W.iperm = (int*)(A + o[21]);
     W.lev_l = (int*)(A + o[22]);
@@ -345,6 +381,8 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     W.pend_aval = (double*)(A + o[44]);
     W.pend_ucol = (int*)(A + o[45]);
     W.pend_uval = (double*)(A + o[46]);
+    W.chunk_meta = (int4*)(A + o[47]);
+    W.lvl_nchunk = (int*)(A + o[48]);
     W.ctl = ctx->dCtl + w;
     const Layout& L = lay[w];
     e = cudaMemcpyAsync((void*)W.Z, L.Z.data(), sizeof(double) * L.Z.size(), cudaMemcpyHostToDevice, ctx->stream);
@@ -558,6 +596,8 @@ extern "C" vmc_status vmc_get_stats(vmc_ctx* ctx, int walker, vmc_stats* out) {
   out->n_updates = h.n_upd;
   out->status = h.status;
   for (int b = 0; b < kHistBins; ++b) out->its_hist[b] = h.hist[b];
+  for (int b = 0; b < 16; ++b) out->phase_cycles[b] = h.cyc[b];
+  out->alg_bytes = h.alg_bytes;
   return VMC_OK;
 }
 
@@ -572,6 +612,8 @@ extern "C" vmc_status vmc_reset_stats(vmc_ctx* ctx) {
     c.refactors_updates = c.factorizations = 0;
     c.N_max_seen = c.N_sum = 0.0;
     for (long long& b : c.hist) b = 0;
+    for (long long& b : c.cyc) b = 0;
+    c.alg_bytes = 0.0;
   }
   CK(cudaMemcpyAsync(ctx->dCtl, h.data(), sizeof(Ctl) * ctx->nw, cudaMemcpyHostToDevice, ctx->stream), "stats");
   CK(cudaStreamSynchronize(ctx->stream), "synchronize");
@@ -646,7 +688,7 @@ extern "C" vmc_status vmc_apply_preconditioner(vmc_ctx* ctx, int walker, const d
   if (!ctx->ready) return fail(ctx, VMC_ERR_STATE, "positions not set");
   const Walker& W = ctx->hw[walker];
   CK(cudaMemcpyAsync(W.r64, v, sizeof(double) * W.n, cudaMemcpyHostToDevice, ctx->stream), "vector");
-  CK(launch_apply_precond(cfg(ctx), ctx->dW, walker), "precond kernel");
+  CK(launch_apply_precond(cfg(ctx), ctx->dW, walker, ctx->P), "precond kernel");
   CK(cudaMemcpyAsync(z, W.x64, sizeof(double) * W.n, cudaMemcpyDeviceToHost, ctx->stream), "vector");
   CK(cudaStreamSynchronize(ctx->stream), "synchronize");
   ctx->pending[walker] = 0;

@@ -30,6 +30,13 @@ constexpr int kMaxRowNZ = 2048;   // ILUTP working-row entries before dropping
 constexpr int kMaxSel = 1024;     // ILUTP candidates of one triangle
 constexpr int kMaxUpd = 128;      // longest preconditioner update chain
 constexpr int kHistBins = 64;
+constexpr int kSlotBytes = 8192;  // one shared-memory ring slot = largest stream chunk
+constexpr int kMaxSlots = 8;      // ring depth (chunks in flight)
+constexpr int kChunkRows = 256;   // rows per chunk at most
+constexpr int kChunkHdr = 80;     // chunk header bytes: int4 + 8 next-chunk descriptors
+// phase indices of Ctl::cyc
+enum : int { PH_BUILD = 0, PH_FIRST = 1, PH_REFINE = 2, PH_FACTOR = 3, PH_REORDER = 4, PH_COMMIT = 5, PH_STEP = 6,
+             PH_TRI = 7, PH_CHAIN = 8, PH_SPMV = 9, PH_ORTH = 10, PH_RESID = 11, PH_ILUTP = 12, PH_LEVELS = 13, PH_TRIWAIT = 14 };
 
 // status codes (mirror vmc_status)
 enum : int {
@@ -46,6 +53,7 @@ struct Ctl {
   int pend_valid, pend_k, pend_alen, pend_ulen;
   int last_pivots;
   int last_breakdown;
+  int nchunk_l, nchunk_u;
   double pend_r[3];
   double pend_ratio;
   double its_sum;
@@ -56,6 +64,9 @@ struct Ctl {
   double N_max_seen, N_sum;
   double nnz_A, nnz_LU;
   long long hist[kHistBins];
+  long long cyc[16];  // clock64 cycles by phase (see vmc_stats.phase_cycles)
+  double alg_bytes;   // compulsory (algorithmic) bytes moved by the solves, counted per phase
+  int upd_nnz;        // total nonzeros of the u vectors in the update chain
 };
 
 // Immutable-per-context description of one walker: sizes and device pointers.
@@ -70,9 +81,14 @@ struct Walker {
   int* row_of_part;
   int* part_of_row;
   int* a_col; double* a_val; float* a_val32; int* a_len;
-  int* l_col; double* l_val64; void* l_valT; int* l_len;
-  int* u_col; double* u_val64; void* u_valT; int* u_len;
-  double* u_dinv64; void* u_dinvT;
+  int* l_col; double* l_val64; int* l_len;
+  int* u_col; double* u_val64; int* u_len;
+  double* u_dinv64;
+  // level-ordered chunk streams of L and U for the staged triangular solves
+  unsigned char* lstream; unsigned char* ustream;
+  int2* lchunk; int2* uchunk;   // per chunk {byte offset, bytes}
+  int4* chunk_meta;             // scratch {first row in level order, rows, entries, level end}
+  int* lvl_nchunk;              // scratch per level
   int* perm; int* iperm;
   int* lev_l; int* lev_u;
   int* l_lvl_ptr; int* l_lvl_rows; int* u_lvl_ptr; int* u_lvl_rows; int* lvl_cur;
@@ -89,13 +105,28 @@ struct Params {
   double drop_tol, permtol;
   int lfil_extra, m, max_restarts, max_updates;
   double inner_rtol, ratio_tol, N_max, slow_factor;
+  int ring_slots;   // shared-memory ring depth for the triangular-solve streams
+  int y_smem;       // 1: the triangular-solve vector lives in shared memory
+  int y_bytes;      // bytes reserved for it (multiple of 128)
+  int dsm_bytes;    // total dynamic shared memory (ILUTP scratch may use all of it)
 };
 
 // Shared memory of a walker CTA (static, < 48 KB).
 struct __align__(16) Shared {
-  double H[(kMaxM + 1) * kMaxM];
-  double g[kMaxM + 1], cs[kMaxM], sn[kMaxM], y[kMaxM];
-  double h1[kMaxM + 2], h2[kMaxM + 2];
+  unsigned long long bar[kMaxSlots];  // mbarriers of the stream ring
+  int ring_seq;                       // chunks consumed so far in this launch
+  union {
+    struct {                          // GMRES
+      double H[(kMaxM + 1) * kMaxM];
+      double g[kMaxM + 1], cs[kMaxM], sn[kMaxM], y[kMaxM];
+      double h1[kMaxM + 2], h2[kMaxM + 2];
+    };
+    struct {                          // ILUTP working row
+      int nz[kMaxRowNZ];
+      int selF[kMaxSel];
+      double selV[kMaxSel];
+    };
+  };
   double red[40];
   double redv[33];
   int redi[33];
@@ -104,14 +135,64 @@ struct __align__(16) Shared {
   int acol[kMaxRow];
   double uval[kMaxU];
   int ucol[kMaxU];
-  int nz[kMaxRowNZ];
-  int selF[kMaxSel];
-  double selV[kMaxSel];
   double cupd[kMaxUpd];
   int alen, ulen;
   int iflag[8];
   double dflag[8];
 };
+
+// ---- dynamic shared memory, mbarriers and bulk (TMA) copies ----------------
+__device__ __forceinline__ unsigned char* dyn_smem() {
+  extern __shared__ __align__(128) unsigned char vmc_dsm[];
+  return vmc_dsm;
+}
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy completing on bar; dst, src 16-byte aligned, bytes % 16 == 0
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of bar to complete; gives up after ~1 s (returns false).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = smem_u32(bar);
+  unsigned ok = 0;
+  asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+               : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+  if (ok) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+    if (ok) return true;
+    if (global_ns() - t0 > 1000000000ull) return false;
+  }
+}
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// Byte layout of one stream chunk (all offsets multiples of 16):
+//   int4 header {rows, entries, level_end, 0}; int2 next[8] (descriptors {offset, bytes}
+//   of the following 8 chunks, {0, 0} past the end); int rows[pad4(r)]; int starts[pad4(r+1)];
+//   int cols[pad4(e)]; T vals[e] (padded to 16 B); U only: T dinv[r] (padded).
+__host__ __device__ __forceinline__ int pad4(int x) { return (x + 3) & ~3; }
+__host__ __device__ __forceinline__ int pad16(int x) { return (x + 15) & ~15; }
+__host__ __device__ __forceinline__ int chunk_bytes(int r, int e, int tsz, bool upper) {
+  return kChunkHdr + 4 * pad4(r) + 4 * pad4(r + 1) + 4 * pad4(e) + pad16(tsz * e) + (upper ? pad16(tsz * r) : 0);
+}
 
 // ---- warp / block reductions (fixed butterfly order: deterministic) ----------
 __device__ __forceinline__ double warp_sum(double v) {
@@ -177,6 +258,44 @@ __device__ __forceinline__ int block_max_int(int v, Shared& sh) {
   const int r = sh.redi[32];
   __syncthreads();
   return r;
+}
+
+// Exclusive prefix sum of a[0..cnt) in place (global or shared); returns the total.
+__device__ __forceinline__ int block_scan_inplace(int* a, int cnt, Shared& sh) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int per = (cnt + nt - 1) / nt;
+  const int b = min(cnt, tid * per), e = min(cnt, b + per);
+  int s = 0;
+  for (int i = b; i < e; ++i) s += a[i];
+  int inc = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) sh.redi[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    int t = lane < nw ? sh.redi[lane] : 0;
+    int ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= o) ti += v;
+    }
+    if (lane < nw) sh.redi[lane] = ti - t;  // exclusive warp offsets
+    if (lane == 31) sh.redi[32] = ti;
+  }
+  __syncthreads();
+  int off = sh.redi[wid] + inc - s;
+  for (int i = b; i < e; ++i) {
+    const int t = a[i];
+    a[i] = off;
+    off += t;
+  }
+  const int total = sh.redi[32];
+  __syncthreads();
+  return total;
 }
 
 // Block argmin of (d, j) in lexicographic order; every thread gets (d, j).

@@ -22,7 +22,9 @@ __device__ __noinline__ void solve_with_controller(const Walker& w, const Params
   Ctl* c = w.ctl;
   const double rtol = P.inner_rtol;
   int brow = w.row_of_part[k];
+  long long t0 = clock64();
   solve_first<T>(w, P, brow, rtol, o, sh);
+  if (threadIdx.x == 0) c->cyc[PH_FIRST] += clock64() - t0;
   int cause = 0;
   const long long cnt = c->its_cnt;
   const double avg = cnt > 0 ? c->its_sum / (double)cnt : 0.0;
@@ -42,15 +44,20 @@ __device__ __noinline__ void solve_with_controller(const Walker& w, const Params
     __syncthreads();
     brow = w.row_of_part[k];
     const int its_before = o.its1;
+    t0 = clock64();
     solve_first<T>(w, P, brow, rtol, o, sh);
+    if (threadIdx.x == 0) c->cyc[PH_FIRST] += clock64() - t0;
     o.total_its += its_before;
   } else if (threadIdx.x == 0) {
     c->its_sum += (double)o.its1;
     c->its_cnt += 1;
   }
   const double floor_rtol = rtol;
+  t0 = clock64();
   refine<T>(w, P, brow, floor_rtol, 2 + P.max_restarts, o, sh);
   if (threadIdx.x == 0) {
+    c->cyc[PH_REFINE] += clock64() - t0;
+    if (sh.iflag[3] && c->status == ST_OK) c->status = ST_TIMEOUT;
     c->solves += cause ? 2 : 1;
     c->inner_its += o.total_its;
     c->first_its += o.its1;
@@ -68,6 +75,7 @@ template <typename T>
 __device__ __noinline__ void commit_move(const Walker& w, const Params& P, int k, double ratio, Shared& sh) {
   const int tid = threadIdx.x, nt = blockDim.x, n = w.n, cap = w.cap;
   const int alen = sh.alen, ulen = sh.ulen;
+  const long long t0 = clock64();
   for (int t = tid; t < alen; t += nt) {
     w.a_col[(size_t)k * cap + t] = sh.acol[t];
     w.a_val[(size_t)k * cap + t] = sh.aval[t];
@@ -91,7 +99,7 @@ __device__ __noinline__ void commit_move(const Walker& w, const Params& P, int k
       w.upd_ucol[(size_t)s * kMaxU + t] = sh.ucol[t];
       Uv[(size_t)s * kMaxU + t] = (T)sh.uval[t];
     }
-    if (tid == 0) w.upd_ulen[s] = ulen;
+    if (tid == 0) { w.upd_ulen[s] = ulen; c->upd_nnz += ulen; }
     __syncthreads();
     // G[s][t] = u_s^T z_hat_t for t < s, from the stored (working-precision) values
     const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
@@ -113,6 +121,7 @@ __device__ __noinline__ void commit_move(const Walker& w, const Params& P, int k
     }
     if (tid == 0 && (fl & 2)) c->status = ST_CAPACITY;
   }
+  if (tid == 0) c->cyc[PH_COMMIT] += clock64() - t0;
   __syncthreads();
 }
 
@@ -148,6 +157,7 @@ __device__ __noinline__ void mc_step(const Walker& w, const Params& P, int k, ui
     }
     return;
   }
+  const long long t_step = clock64();
   if (threadIdx.x == 0) {
     double z[3];
     normal3(seed, sweep, (uint32_t)k, 1u, z);
@@ -155,6 +165,7 @@ __device__ __noinline__ void mc_step(const Walker& w, const Params& P, int k, ui
   }
   __syncthreads();
   if (!build_move(w, k, sh)) return;
+  if (threadIdx.x == 0) c->cyc[PH_BUILD] += clock64() - t_step;
   SolveOut o;
   solve_with_controller<T>(w, P, k, o, sh);
   const double U = accept_uniform(seed, sweep, (uint32_t)k);
@@ -167,6 +178,7 @@ __device__ __noinline__ void mc_step(const Walker& w, const Params& P, int k, ui
     c->accepts += acc ? 1 : 0;
   }
   if (acc) commit_move<T>(w, P, k, o.ratio, sh);
+  if (threadIdx.x == 0) c->cyc[PH_STEP] += clock64() - t_step;
   __syncthreads();
 }
 
@@ -178,6 +190,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_sweep(const Walker* __restrict_
                                                 long long sweep0, double sigma, const uint64_t* __restrict__ seeds,
                                                 uint8_t* acc_log, double* ratio_log) {
   __shared__ Shared sh;
+  ring_init(sh, P);
   const int wi = walker0 + blockIdx.x;
   const Walker& w = W[wi];
   const uint64_t seed = seeds[wi];
@@ -199,6 +212,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_step(const Walker* __restrict__
   const int wi = walker0 + blockIdx.x;
   const Walker& w = W[wi];
   if (q >= w.n) return;
+  ring_init(sh, P);
   const long long idx = (long long)n_sweeps * w.log_base + (long long)s_local * w.n + q;
   mc_step<T>(w, P, q, seeds[wi], (uint32_t)(sweep0 + s_local), sigma, acc_log ? acc_log + idx : nullptr,
              ratio_log ? ratio_log + idx : nullptr, sh);
@@ -209,6 +223,7 @@ template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_ratio(const Walker* __restrict__ W, int wi, Params P, int k, double rx,
                                                 double ry, double rz) {
   __shared__ Shared sh;
+  ring_init(sh, P);
   const Walker& w = W[wi];
   Ctl* c = w.ctl;
   if (threadIdx.x == 0) {
@@ -237,6 +252,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_ratio(const Walker* __restrict_
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_accept(const Walker* __restrict__ W, int wi, Params P) {
   __shared__ Shared sh;
+  ring_init(sh, P);
   const Walker& w = W[wi];
   Ctl* c = w.ctl;
   const int valid = c->pend_valid;
@@ -270,6 +286,7 @@ __global__ void k_init_positions(const Walker* __restrict__ W, const uint64_t* _
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_setup(const Walker* __restrict__ W, int walker0, Params P) {
   __shared__ Shared sh;
+  ring_init(sh, P);
   const Walker& w = W[walker0 + blockIdx.x];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   Ctl* c = w.ctl;
@@ -303,20 +320,22 @@ __global__ void __launch_bounds__(kMaxThreads) k_setup(const Walker* __restrict_
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_refactor(const Walker* __restrict__ W, int wi, Params P, int reorder) {
   __shared__ Shared sh;
+  ring_init(sh, P);
   const Walker& w = W[wi];
   factor_block<T>(w, P, sh, reorder != 0);
 }
 
 // z = M v for the test entry point: v in r64 (FP64), result in x64 (FP64).
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) k_apply_precond(const Walker* __restrict__ W, int wi) {
+__global__ void __launch_bounds__(kMaxThreads) k_apply_precond(const Walker* __restrict__ W, int wi, Params P) {
   __shared__ Shared sh;
   const Walker& w = W[wi];
+  ring_init(sh, P);
   T* V = (T*)w.V;
   T* Zk = (T*)w.Zk;
   for (int i = threadIdx.x; i < w.n; i += blockDim.x) V[i] = (T)w.r64[i];
   __syncthreads();
-  precond_apply<T>(w, V, Zk, sh);
+  precond_apply<T>(w, P, V, Zk, sh);
   for (int i = threadIdx.x; i < w.n; i += blockDim.x) w.x64[i] = (double)Zk[i];
 }
 
@@ -333,60 +352,60 @@ __global__ void k_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-template <typename T>
-static cudaError_t launch_sweep_t(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P,
-                                  int n_sweeps, long long sweep0, double sigma, const uint64_t* seeds, uint8_t* acc,
-                                  double* ratio) {
-  k_sweep<T><<<nwalk, L.threads, 0, L.stream>>>(W, walker0, P, n_sweeps, sweep0, sigma, seeds, acc, ratio);
-  return cudaGetLastError();
+template <typename K>
+static cudaError_t prep(K kernel, const LaunchCfg& L) {
+  if (L.smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+  return cudaSuccess;
 }
-template <typename T>
-static cudaError_t launch_step_t(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int q,
-                                 int n_sweeps, int s_local, long long sweep0, double sigma, const uint64_t* seeds,
-                                 uint8_t* acc, double* ratio) {
-  k_step<T><<<nwalk, L.threads, 0, L.stream>>>(W, walker0, P, q, n_sweeps, s_local, sweep0, sigma, seeds, acc, ratio);
-  return cudaGetLastError();
+#define VMC_LAUNCH(KERNEL, GRID, ...)                                   \
+  do {                                                                 \
+    cudaError_t e_ = prep(KERNEL, L);                                  \
+    if (e_ != cudaSuccess) return e_;                                  \
+    KERNEL<<<(GRID), L.threads, L.smem, L.stream>>>(__VA_ARGS__);      \
+    return cudaGetLastError();                                         \
+  } while (0)
+
+int kernel_static_smem(bool fp64) {
+  cudaFuncAttributes a{};
+  if (fp64) cudaFuncGetAttributes(&a, k_sweep<double>);
+  else cudaFuncGetAttributes(&a, k_sweep<float>);
+  return (int)a.sharedSizeBytes;
 }
 
 cudaError_t launch_sweep(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int n_sweeps,
                          long long sweep0, double sigma, const uint64_t* seeds, uint8_t* acc, double* ratio) {
-  return L.fp64 ? launch_sweep_t<double>(L, W, walker0, nwalk, P, n_sweeps, sweep0, sigma, seeds, acc, ratio)
-                : launch_sweep_t<float>(L, W, walker0, nwalk, P, n_sweeps, sweep0, sigma, seeds, acc, ratio);
+  if (L.fp64) VMC_LAUNCH(k_sweep<double>, nwalk, W, walker0, P, n_sweeps, sweep0, sigma, seeds, acc, ratio);
+  VMC_LAUNCH(k_sweep<float>, nwalk, W, walker0, P, n_sweeps, sweep0, sigma, seeds, acc, ratio);
 }
 cudaError_t launch_step(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int q,
                         int n_sweeps, int s_local, long long sweep0, double sigma, const uint64_t* seeds,
                         uint8_t* acc, double* ratio) {
-  return L.fp64 ? launch_step_t<double>(L, W, walker0, nwalk, P, q, n_sweeps, s_local, sweep0, sigma, seeds, acc, ratio)
-                : launch_step_t<float>(L, W, walker0, nwalk, P, q, n_sweeps, s_local, sweep0, sigma, seeds, acc, ratio);
+  if (L.fp64) VMC_LAUNCH(k_step<double>, nwalk, W, walker0, P, q, n_sweeps, s_local, sweep0, sigma, seeds, acc, ratio);
+  VMC_LAUNCH(k_step<float>, nwalk, W, walker0, P, q, n_sweeps, s_local, sweep0, sigma, seeds, acc, ratio);
 }
 cudaError_t launch_ratio(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int k, const double r[3]) {
-  if (L.fp64) k_ratio<double><<<1, L.threads, 0, L.stream>>>(W, wi, P, k, r[0], r[1], r[2]);
-  else k_ratio<float><<<1, L.threads, 0, L.stream>>>(W, wi, P, k, r[0], r[1], r[2]);
-  return cudaGetLastError();
+  if (L.fp64) VMC_LAUNCH(k_ratio<double>, 1, W, wi, P, k, r[0], r[1], r[2]);
+  VMC_LAUNCH(k_ratio<float>, 1, W, wi, P, k, r[0], r[1], r[2]);
 }
 cudaError_t launch_accept(const LaunchCfg& L, const Walker* W, int wi, const Params& P) {
-  if (L.fp64) k_accept<double><<<1, L.threads, 0, L.stream>>>(W, wi, P);
-  else k_accept<float><<<1, L.threads, 0, L.stream>>>(W, wi, P);
-  return cudaGetLastError();
+  if (L.fp64) VMC_LAUNCH(k_accept<double>, 1, W, wi, P);
+  VMC_LAUNCH(k_accept<float>, 1, W, wi, P);
 }
 cudaError_t launch_init_positions(const LaunchCfg& L, const Walker* W, int nwalk, const uint64_t* seeds, double jitter) {
   k_init_positions<<<nwalk, 256, 0, L.stream>>>(W, seeds, jitter);
   return cudaGetLastError();
 }
 cudaError_t launch_setup(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P) {
-  if (L.fp64) k_setup<double><<<nwalk, L.threads, 0, L.stream>>>(W, walker0, P);
-  else k_setup<float><<<nwalk, L.threads, 0, L.stream>>>(W, walker0, P);
-  return cudaGetLastError();
+  if (L.fp64) VMC_LAUNCH(k_setup<double>, nwalk, W, walker0, P);
+  VMC_LAUNCH(k_setup<float>, nwalk, W, walker0, P);
 }
 cudaError_t launch_refactor(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int reorder) {
-  if (L.fp64) k_refactor<double><<<1, L.threads, 0, L.stream>>>(W, wi, P, reorder);
-  else k_refactor<float><<<1, L.threads, 0, L.stream>>>(W, wi, P, reorder);
-  return cudaGetLastError();
+  if (L.fp64) VMC_LAUNCH(k_refactor<double>, 1, W, wi, P, reorder);
+  VMC_LAUNCH(k_refactor<float>, 1, W, wi, P, reorder);
 }
-cudaError_t launch_apply_precond(const LaunchCfg& L, const Walker* W, int wi) {
-  if (L.fp64) k_apply_precond<double><<<1, L.threads, 0, L.stream>>>(W, wi);
-  else k_apply_precond<float><<<1, L.threads, 0, L.stream>>>(W, wi);
-  return cudaGetLastError();
+cudaError_t launch_apply_precond(const LaunchCfg& L, const Walker* W, int wi, const Params& P) {
+  if (L.fp64) VMC_LAUNCH(k_apply_precond<double>, 1, W, wi, P);
+  VMC_LAUNCH(k_apply_precond<float>, 1, W, wi, P);
 }
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, cudaStream_t s) {
   k_philox<<<(n + 127) / 128, 128, 0, s>>>(ctr, key, out, n);

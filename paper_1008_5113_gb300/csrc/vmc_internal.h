@@ -14,7 +14,10 @@ struct LaunchCfg {
   cudaStream_t stream;
   int threads;
   bool fp64;
+  size_t smem;  // dynamic shared memory per walker CTA
 };
+// static shared memory of the walker kernels (bytes)
+int kernel_static_smem(bool fp64);
 
 cudaError_t launch_sweep(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int n_sweeps,
                          long long sweep0, double sigma, const uint64_t* seeds, uint8_t* acc, double* ratio);
@@ -26,7 +29,7 @@ cudaError_t launch_accept(const LaunchCfg& L, const Walker* W, int wi, const Par
 cudaError_t launch_init_positions(const LaunchCfg& L, const Walker* W, int nwalk, const uint64_t* seeds, double jitter);
 cudaError_t launch_setup(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P);
 cudaError_t launch_refactor(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int reorder);
-cudaError_t launch_apply_precond(const LaunchCfg& L, const Walker* W, int wi);
+cudaError_t launch_apply_precond(const LaunchCfg& L, const Walker* W, int wi, const Params& P);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, cudaStream_t s);
 
 // host-side geometry and layout (vmc_layout.cpp)

@@ -38,42 +38,104 @@ __device__ __forceinline__ void spmv(const Walker& w, const T* __restrict__ x, T
   }
 }
 
+// Shared-memory ring of the stream chunks: one mbarrier per slot, initialised once
+// per kernel launch; chunk g of the launch lives in slot g % S, phase (g / S) & 1.
+__device__ __forceinline__ void ring_init(Shared& sh, const Params& P) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P.ring_slots; ++s) mbar_init(&sh.bar[s], 1);
+    sh.ring_seq = 0;
+    sh.iflag[3] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+// One triangular solve in place on y (shared or global), streaming the factor's
+// chunks through the ring with bulk copies issued ring_slots chunks ahead.
+// Lower: y_r -= sum_t L_rt y_t.  Upper: y_r = (y_r - sum_t U_rt y_t) / U_rr.
+template <typename T>
+__device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, bool upper, T* y, Shared& sh) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const unsigned char* stream = upper ? w.ustream : w.lstream;
+  const int2* tab = upper ? w.uchunk : w.lchunk;
+  const int nch = upper ? w.ctl->nchunk_u : w.ctl->nchunk_l;
+  const int S = P.ring_slots;
+  unsigned char* ring = dyn_smem() + P.y_bytes;
+  const int seq0 = sh.ring_seq;
+  if (tid == 0) {
+    const int pre = min(S, nch);
+    for (int c = 0; c < pre; ++c) {
+      const int slot = (seq0 + c) % S;
+      const int2 tc = tab[c];
+      mbar_expect_tx(&sh.bar[slot], (unsigned)tc.y);
+      bulk_g2s(ring + (size_t)slot * kSlotBytes, stream + tc.x, (unsigned)tc.y, &sh.bar[slot]);
+    }
+  }
+  for (int c = 0; c < nch; ++c) {
+    const int g = seq0 + c;
+    const int slot = g % S;
+    const long long tw = clock64();
+    if (!mbar_wait(&sh.bar[slot], (unsigned)((g / S) & 1))) sh.iflag[3] = 1;
+    if (tid == 0) w.ctl->cyc[PH_TRIWAIT] += clock64() - tw;
+    const unsigned char* ch = ring + (size_t)slot * kSlotBytes;
+    const int4 hd = *(const int4*)ch;
+    const int nr = hd.x, ne = hd.y;
+    const int* rws = (const int*)(ch + kChunkHdr);
+    const int* st = rws + pad4(nr);
+    const int* cl = st + pad4(nr + 1);
+    const T* vl = (const T*)(cl + pad4(ne));
+    const T* dv = (const T*)((const unsigned char*)vl + pad16((int)sizeof(T) * ne));
+    // G lanes per row (G a power of two, as large as the chunk's row count allows),
+    // each lane a strided slice of the row, then a G-lane shuffle reduction
+    int G = 1;
+    while (G < 32 && (G << 1) * nr <= nt) G <<= 1;
+    const int gid = tid / G, gl = tid & (G - 1), ng = nt / G;
+    for (int base = 0; base < nr; base += ng) {
+      const int i = base + gid;
+      const bool valid = i < nr;
+      T part = 0;
+      int r = 0;
+      if (valid) {
+        r = rws[i];
+        const int e = st[i + 1];
+        for (int t = st[i] + gl; t < e; t += G) part += vl[t] * y[cl[t]];
+      }
+      for (int o = G >> 1; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (valid && gl == 0) {
+        T acc = y[r] - part;
+        if (upper) acc *= dv[i];
+        y[r] = acc;
+      }
+    }
+    // descriptor of chunk c + S, read from this chunk's header before the slot is reused
+    const int2 nx = (tid == 0 && c + S < nch) ? ((const int2*)(ch + 16))[S - 1] : make_int2(0, 0);
+    __syncthreads();
+    if (tid == 0 && c + S < nch) {
+      mbar_expect_tx(&sh.bar[slot], (unsigned)nx.y);
+      bulk_g2s(ring + (size_t)slot * kSlotBytes, stream + nx.x, (unsigned)nx.y, &sh.bar[slot]);
+    }
+  }
+  if (tid == 0) sh.ring_seq = seq0 + nch;
+  __syncthreads();
+}
+
 // z = M v  (v indexed by rows, z by columns of A_p).  Block-wide, ends synchronised.
 template <typename T>
-__device__ __noinline__ void precond_apply(const Walker& w, const T* __restrict__ v, T* __restrict__ z, Shared& sh) {
-  const int n = w.n, tid = threadIdx.x, nt = blockDim.x, capLU = w.capLU;
-  T* y = (T*)w.tv;
-  const T* lv = (const T*)w.l_valT;
-  const T* uv = (const T*)w.u_valT;
-  const T* dv = (const T*)w.u_dinvT;
+__device__ __noinline__ void precond_apply(const Walker& w, const Params& P, const T* __restrict__ v,
+                                           T* __restrict__ z, Shared& sh) {
+  const int n = w.n, tid = threadIdx.x, nt = blockDim.x;
+  T* y = P.y_smem ? (T*)dyn_smem() : (T*)w.tv;
+  const long long t0 = clock64();
   for (int i = tid; i < n; i += nt) y[i] = v[i];
   __syncthreads();
-  const int nll = w.ctl->nlev_l, nlu = w.ctl->nlev_u;
-  for (int lev = 0; lev < nll; ++lev) {
-    const int b = w.l_lvl_ptr[lev], e = w.l_lvl_ptr[lev + 1];
-    for (int q = b + tid; q < e; q += nt) {
-      const int r = w.l_lvl_rows[q];
-      const int len = w.l_len[r];
-      const int* c = w.l_col + (size_t)r * capLU;
-      const T* vv = lv + (size_t)r * capLU;
-      T acc = y[r];
-      for (int t = 0; t < len; ++t) acc -= vv[t] * y[c[t]];
-      y[r] = acc;
-    }
-    __syncthreads();
-  }
-  for (int lev = 0; lev < nlu; ++lev) {
-    const int b = w.u_lvl_ptr[lev], e = w.u_lvl_ptr[lev + 1];
-    for (int q = b + tid; q < e; q += nt) {
-      const int r = w.u_lvl_rows[q];
-      const int len = w.u_len[r];
-      const int* c = w.u_col + (size_t)r * capLU;
-      const T* vv = uv + (size_t)r * capLU;
-      T acc = y[r];
-      for (int t = 0; t < len; ++t) acc -= vv[t] * y[c[t]];
-      y[r] = acc * dv[r];
-    }
-    __syncthreads();
+  tri_staged<T>(w, P, false, y, sh);
+  tri_staged<T>(w, P, true, y, sh);
+  const long long t1 = clock64();
+  if (tid == 0) {
+    Ctl* c = w.ctl;
+    c->cyc[PH_TRI] += t1 - t0;
+    // factor values + indices, diagonal, v read, z write, the level-row records
+    c->alg_bytes += c->nnz_LU * (sizeof(T) + 4) + (double)n * (3 * sizeof(T) + 8);
   }
   for (int t = tid; t < n; t += nt) z[w.perm[t]] = y[t];
   __syncthreads();
@@ -91,13 +153,26 @@ __device__ __noinline__ void precond_apply(const Walker& w, const T* __restrict_
       acc = warp_sum(acc);
       if (lane == 0) sh.cupd[s] = acc;
     }
+    // G[0..mu)[0..mu) staged in the (now idle) stream ring when it fits, then
+    // c_s = d_s - sum_{t<s} G[s][t] c_t by warp 0
+    const bool gs_smem = (size_t)mu * mu * sizeof(double) <= (size_t)P.ring_slots * kSlotBytes;
+    double* Gs = gs_smem ? (double*)(dyn_smem() + P.y_bytes) : w.upd_G;
+    const int gld = gs_smem ? mu : kMaxUpd;
+    if (gs_smem) {
+      for (int idx = tid; idx < mu * mu; idx += nt) {
+        const int s = idx / mu, t = idx - s * mu;
+        if (t < s) Gs[idx] = w.upd_G[(size_t)s * kMaxUpd + t];
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // ring is refilled by bulk copies later
+    }
     __syncthreads();
-    if (tid == 0) {                             // c_s = d_s - sum_{t<s} G[s][t] c_t
-      const double* G = w.upd_G;
+    if (wid == 0) {
       for (int s = 1; s < mu; ++s) {
-        double acc = sh.cupd[s];
-        for (int t = 0; t < s; ++t) acc -= G[(size_t)s * kMaxUpd + t] * sh.cupd[t];
-        sh.cupd[s] = acc;
+        double acc = 0.0;
+        for (int t = lane; t < s; t += 32) acc += Gs[(size_t)s * gld + t] * sh.cupd[t];
+        acc = warp_sum(acc);
+        if (lane == 0) sh.cupd[s] -= acc;
+        __syncwarp();
       }
     }
     __syncthreads();
@@ -107,6 +182,12 @@ __device__ __noinline__ void precond_apply(const Walker& w, const T* __restrict_
       z[i] = acc;
     }
     __syncthreads();
+  }
+  if (tid == 0) {
+    Ctl* c = w.ctl;
+    c->cyc[PH_CHAIN] += clock64() - t1;
+    // z_hat vectors, sparse u vectors, z read + write
+    if (mu > 0) c->alg_bytes += (double)mu * n * sizeof(T) + (double)c->upd_nnz * (sizeof(T) + 4) + 2.0 * n * sizeof(T);
   }
 }
 
@@ -152,9 +233,19 @@ __device__ __noinline__ int gmres_inner(const Walker& w, const Params& P, double
     T* vj = V + (size_t)j * n;
     T* zj = Zk + (size_t)j * n;
     T* wv = V + (size_t)(j + 1) * n;
-    precond_apply<T>(w, vj, zj, sh);
+    precond_apply<T>(w, P, vj, zj, sh);
+    const long long ts = clock64();
     spmv<T>(w, zj, wv);
     __syncthreads();
+    const long long to = clock64();
+    if (tid == 0) {
+      Ctl* c = w.ctl;
+      c->cyc[PH_SPMV] += to - ts;
+      // SpMV: values + indices, x read, y write; CGS2: two projection passes over
+      // V_0..V_j and w, two update passes, the normalisation
+      c->alg_bytes += c->nnz_A * (sizeof(T) + 4) + (double)n * (2 * sizeof(T) + 4) +
+                      (double)n * sizeof(T) * (4.0 * (j + 1) + 8.0);
+    }
     multi_dot<T>(V, n, j + 1, wv, sh.h1, true);          // projections + monitor
     mon2 = fmax(mon2, sh.h1[j + 1]);
     for (int i = tid; i < n; i += nt) {
@@ -192,6 +283,7 @@ __device__ __noinline__ int gmres_inner(const Walker& w, const Params& P, double
       sh.g[j + 1] = -sh.sn[j] * sh.g[j];
       sh.g[j] = sh.cs[j] * sh.g[j];
       sh.iflag[1] = (fabs(sh.g[j + 1]) <= rtol * beta) || nrm == 0.0;
+      w.ctl->cyc[PH_ORTH] += clock64() - to;
     }
     __syncthreads();
     ++j;
@@ -213,6 +305,7 @@ __device__ __noinline__ int gmres_inner(const Walker& w, const Params& P, double
     for (int k = 0; k < j; ++k) acc += (T)sh.y[k] * Zk[(size_t)k * n + i];
     w.x64[i] += (double)acc;
   }
+  if (tid == 0) w.ctl->alg_bytes += (double)n * (j * sizeof(T) + 16.0);  // Zk y, x read + write
   __syncthreads();
   return j;
 }
@@ -221,6 +314,7 @@ __device__ __noinline__ int gmres_inner(const Walker& w, const Params& P, double
 // Ends synchronised.
 __device__ __forceinline__ double residual64(const Walker& w, int brow, double* xnorm, Shared& sh) {
   const int n = w.n, cap = w.cap;
+  const long long t0 = clock64();
   double ss = 0.0, xx = 0.0;
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
     const int p = w.part_of_row[r];
@@ -236,7 +330,13 @@ __device__ __forceinline__ double residual64(const Walker& w, int brow, double* 
     xx += xr * xr;
   }
   *xnorm = sqrt(block_sum(xx, sh));
-  return sqrt(block_sum(ss, sh));
+  const double rn = sqrt(block_sum(ss, sh));
+  if (threadIdx.x == 0) {
+    Ctl* c = w.ctl;
+    c->cyc[PH_RESID] += clock64() - t0;
+    c->alg_bytes += c->nnz_A * 12.0 + (double)n * 24.0;  // FP64 A, x read, r write, row lengths
+  }
+  return rn;
 }
 
 // u^T x64 over the u list in shared memory (FP64).

@@ -82,9 +82,63 @@ __device__ __forceinline__ bool sel_keep(const Shared& sh, int c, int e, int kee
 // Returns: bit 0 breakdown (zero pivot replaced by (1e-4 + tau) ||a_i||), bit 1
 // capacity overflow.
 // ---------------------------------------------------------------------------
+template <typename T>
 __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared& sh, int* npiv_out, double* nnz_out,
-                          int* p_out) {
+                                       int* p_out) {
   const int n = w.n, lane = threadIdx.x & 31, cap = w.cap, capLU = w.capLU;
+  // Working arrays in the dynamic shared memory (idle while factoring) when they fit:
+  // wrow (dense work row), wpos (its slot map), iperm, then U diagonal inverses,
+  // U lengths and L levels.  Otherwise the global copies are used.
+  const size_t dbytes = (size_t)P.dsm_bytes;
+  unsigned char* dsm = dyn_smem();
+  double* wrow = w.wrow;
+  int* wpos = w.wpos;
+  int* iperm = w.iperm;
+  double* udinv = w.u_dinv64;
+  int* ulen_a = w.u_len;
+  int* levl = w.lev_l;
+  const bool sm_work = (size_t)16 * n <= dbytes;
+  const bool sm_rows = (size_t)32 * n <= dbytes;
+  if (sm_work) {
+    wrow = (double*)dsm;
+    wpos = (int*)(wrow + n);
+    iperm = wpos + n;
+  }
+  if (sm_rows) {
+    udinv = (double*)(dsm + (size_t)16 * n);
+    ulen_a = (int*)(udinv + n);
+    levl = ulen_a + n;
+  }
+  // Cache of finished U rows (original labels; values in the working precision):
+  // row r at ucc/ucv[uoff[r] .. uoff[r] + len), uoff[r] = -1 when not cached.
+  int* uoff = nullptr;
+  int* ucc = nullptr;
+  T* ucv = nullptr;
+  int ucap = 0, ufill = 0;
+  // Pending L-part labels of the current row: a bitmap over labels (one bit per
+  // label) with a summary word per 32 bitmap words, so that the next label to
+  // eliminate is found with two warp-wide word scans instead of a scan of the row.
+  const int nwords = (n + 31) >> 5;
+  const int nsum = (nwords + 31) >> 5;
+  unsigned* lbits = nullptr;
+  unsigned* lsum = nullptr;
+  const size_t bm_bytes = 4 * (size_t)(pad4(nwords) + pad4(nsum));
+  if (sm_rows && (size_t)32 * n + bm_bytes <= dbytes) {
+    lbits = (unsigned*)(dsm + (size_t)32 * n);
+    lsum = lbits + pad4(nwords);
+  }
+  const size_t cache_at = (size_t)32 * n + bm_bytes;
+  if (lbits && cache_at + (size_t)4 * n + 16 + 64 * (sizeof(T) + 4) <= dbytes) {
+    uoff = (int*)(dsm + cache_at);
+    const size_t rest = dbytes - cache_at - (size_t)4 * pad4(n + 1);
+    ucap = (int)(rest / (sizeof(T) + 4)) & ~3;
+    ucc = uoff + pad4(n + 1);
+    ucv = (T*)(ucc + ucap);
+  }
+  if (lbits) {
+    for (int i = lane; i < nwords; i += 32) lbits[i] = 0u;
+    for (int i = lane; i < nsum; i += 32) lsum[i] = 0u;
+  }
   int p = P.lfil_extra;
   if (p < 0) {
     long long tot = 0;
@@ -95,7 +149,7 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
   p = min(p, (capLU - 2) / 2);
   const int pk = max(0, min(p, capLU - 2 - cap));  // never exceeds the row capacity
   for (int i = lane; i < n; i += 32) {
-    w.perm[i] = i; w.iperm[i] = i; w.wpos[i] = -1; w.wrow[i] = 0.0; w.lev_l[i] = 0;
+    w.perm[i] = i; iperm[i] = i; wpos[i] = -1; wrow[i] = 0.0; levl[i] = 0;
   }
   __syncwarp();
   int npiv = 0, flags = 0;
@@ -108,14 +162,18 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
     double ss = 0.0;
     int nl = 0, nu = 0;
     for (int t = lane; t < len; t += 32) {
-      const int f = w.iperm[ac[t]];
+      const int f = iperm[ac[t]];
       const double v = av[t];
-      w.wrow[f] = v;
-      w.wpos[f] = t;
+      wrow[f] = v;
+      wpos[f] = t;
       sh.nz[t] = f;
       ss += v * v;
       nl += f < r;
       nu += f > r;
+      if (lbits && f < r) {
+        atomicOr(&lbits[f >> 5], 1u << (f & 31));
+        atomicOr(&lsum[f >> 10], 1u << ((f >> 5) & 31));
+      }
     }
     ss = warp_sum(ss);
     nl = warp_sum_int(nl);
@@ -128,38 +186,72 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
     int last = -1;
     for (;;) {
       int best = 0x7fffffff;
-      for (int t = lane; t < cnt; t += 32) {
-        const int f = sh.nz[t];
-        if (f > last && f < r && f < best) best = f;
+      if (lbits) {
+        __syncwarp();
+        // next pending label > last: first the rest of last's word, then the summary
+        const int w0 = (last + 1) >> 5;
+        unsigned cur = w0 < nwords ? lbits[w0] & (0xffffffffu << ((last + 1) & 31)) : 0u;
+        if (w0 < nwords && (last + 1) >= 0 && cur) {
+          best = (w0 << 5) + __ffs(cur) - 1;
+        } else {
+          const int s0 = (w0 + 1) >> 5;  // summary word holding bitmap word w0 + 1
+          for (int sb = s0; sb < nsum && best == 0x7fffffff; sb += 32) {
+            const int si = sb + lane;
+            unsigned sv = si < nsum ? lsum[si] : 0u;
+            if (si == s0) sv &= 0xffffffffu << ((w0 + 1) & 31);
+            const unsigned any = __ballot_sync(0xffffffffu, sv != 0u);
+            if (any) {
+              const int src = __ffs(any) - 1;
+              const unsigned svs = __shfl_sync(0xffffffffu, sv, src);
+              const int word = ((sb + src) << 5) + __ffs(svs) - 1;
+              best = (word << 5) + __ffs(lbits[word]) - 1;
+            }
+          }
+        }
+        if (best >= r) best = 0x7fffffff;
+      } else {
+        for (int t = lane; t < cnt; t += 32) {
+          const int f = sh.nz[t];
+          if (f > last && f < r && f < best) best = f;
+        }
+        best = warp_min_int(best);
       }
-      best = warp_min_int(best);
       if (best == 0x7fffffff) break;
       last = best;
-      const double wk = w.wrow[best] * w.u_dinv64[best];
+      const double wk = wrow[best] * udinv[best];
       __syncwarp();
       if (fabs(wk) < thr) {
-        if (lane == 0) w.wrow[best] = 0.0;  // dropped multiplier
+        if (lane == 0) wrow[best] = 0.0;  // dropped multiplier
         __syncwarp();
         continue;
       }
-      if (lane == 0) w.wrow[best] = wk;
-      const int ul = w.u_len[best];
-      const int* uc = w.u_col + (size_t)best * capLU;
-      const double* uv = w.u_val64 + (size_t)best * capLU;
+      if (lane == 0) wrow[best] = wk;
+      const int ul = ulen_a[best];
+      const int ub = uoff ? uoff[best] : -1;
       for (int base = 0; base < ul; base += 32) {
         const int t = base + lane;
         const bool valid = t < ul;
         int f = 0;
         double v = 0.0;
         bool exists = false;
-        if (valid) { f = w.iperm[uc[t]]; v = uv[t]; exists = w.wpos[f] >= 0; }
+        if (valid) {
+          if (ub >= 0) { f = iperm[ucc[ub + t]]; v = (double)ucv[ub + t]; }
+          else { f = iperm[w.u_col[(size_t)best * capLU + t]]; v = w.u_val64[(size_t)best * capLU + t]; }
+          exists = wpos[f] >= 0;
+        }
         const unsigned nm = __ballot_sync(0xffffffffu, valid && !exists);
         const int slot = cnt + __popc(nm & lanemask_lt());
         if (valid) {
           if (!exists) {
-            if (slot < kMaxRowNZ) { sh.nz[slot] = f; w.wpos[f] = slot; w.wrow[f] = -wk * v; }
+            if (slot < kMaxRowNZ) {
+              sh.nz[slot] = f; wpos[f] = slot; wrow[f] = -wk * v;
+              if (lbits && f < r) {
+                atomicOr(&lbits[f >> 5], 1u << (f & 31));
+                atomicOr(&lsum[f >> 10], 1u << ((f >> 5) & 31));
+              }
+            }
           } else {
-            w.wrow[f] -= wk * v;
+            wrow[f] -= wk * v;
           }
         }
         cnt += __popc(nm);
@@ -174,7 +266,7 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
       bool c = false;
       int f = 0;
       double v = 0.0;
-      if (t < cnt) { f = sh.nz[t]; v = w.wrow[f]; c = f < r && v != 0.0; }
+      if (t < cnt) { f = sh.nz[t]; v = wrow[f]; c = f < r && v != 0.0; }
       const unsigned m = __ballot_sync(0xffffffffu, c);
       const int slot = cL + __popc(m & lanemask_lt());
       if (c && slot < kMaxSel) { sh.selF[slot] = f; sh.selV[slot] = v; }
@@ -192,7 +284,7 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
       if (k && slot < capLU) {
         w.l_col[(size_t)r * capLU + slot] = sh.selF[e];
         w.l_val64[(size_t)r * capLU + slot] = sh.selV[e];
-        levmax = max(levmax, w.lev_l[sh.selF[e]]);
+        levmax = max(levmax, levl[sh.selF[e]]);
       }
       nL += __popc(m);
     }
@@ -200,14 +292,14 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
     if (nL > capLU) { flags |= 2; nL = capLU; }
     __syncwarp();
     // --- U part: entries above threshold, keep the nu + p largest ---
-    double dval = w.wpos[r] >= 0 ? w.wrow[r] : 0.0;
+    double dval = wpos[r] >= 0 ? wrow[r] : 0.0;
     int cU = 0;
     for (int base = 0; base < cnt; base += 32) {
       const int t = base + lane;
       bool c = false;
       int f = 0;
       double v = 0.0;
-      if (t < cnt) { f = sh.nz[t]; v = w.wrow[f]; c = f > r && fabs(v) >= thr && v != 0.0; }
+      if (t < cnt) { f = sh.nz[t]; v = wrow[f]; c = f > r && fabs(v) >= thr && v != 0.0; }
       const unsigned m = __ballot_sync(0xffffffffu, c);
       const int slot = cU + __popc(m & lanemask_lt());
       if (c && slot < kMaxSel) { sh.selF[slot] = f; sh.selV[slot] = v; }
@@ -248,11 +340,11 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
     if (jm >= 0) {
       // the column labelled jm becomes the diagonal; the old diagonal value moves
       // to label jm (a U-part entry, or nothing if it was zero)
-      newdiag = w.wrow[jm];
+      newdiag = wrow[jm];
       if (lane == 0) {
         const int cr = w.perm[r], cj = w.perm[jm];
         w.perm[r] = cj; w.perm[jm] = cr;
-        w.iperm[cj] = r; w.iperm[cr] = jm;
+        iperm[cj] = r; iperm[cr] = jm;
       }
       ++npiv;
     }
@@ -272,35 +364,156 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
       const unsigned m = __ballot_sync(0xffffffffu, k);
       const int slot = nU + __popc(m & lanemask_lt());
       if (k && slot < capLU) {
-        w.u_col[(size_t)r * capLU + slot] = w.perm[f];  // original column label
+        const int oc = w.perm[f];  // original column label
+        w.u_col[(size_t)r * capLU + slot] = oc;
         w.u_val64[(size_t)r * capLU + slot] = v;
+        if (uoff && ufill + slot < ucap) { ucc[ufill + slot] = oc; ucv[ufill + slot] = (T)v; }
       }
       nU += __popc(m);
     }
     if (nU > capLU) { flags |= 2; nU = capLU; }
+    if (uoff) {
+      if (lane == 0) uoff[r] = ufill + nU <= ucap ? ufill : -1;
+      if (ufill + nU <= ucap) ufill += nU;
+    }
     if (newdiag == 0.0) {
       newdiag = (1e-4 + P.drop_tol) * (norm > 0.0 ? norm : 1.0);
       flags |= 1;
     }
     if (lane == 0) {
       w.l_len[r] = nL;
-      w.u_len[r] = nU;
-      w.u_dinv64[r] = 1.0 / newdiag;
-      w.lev_l[r] = levmax + 1;
+      ulen_a[r] = nU;
+      udinv[r] = 1.0 / newdiag;
+      levl[r] = levmax + 1;
     }
     nnz += (double)(nL + nU + 1);
-    // clear the working row
+    // clear the working row (and the pending-label bitmaps)
     for (int t = lane; t < cnt; t += 32) {
       const int f = sh.nz[t];
-      w.wpos[f] = -1;
-      w.wrow[f] = 0.0;
+      wpos[f] = -1;
+      wrow[f] = 0.0;
+      if (lbits && f < r) { lbits[f >> 5] = 0u; lsum[f >> 10] = 0u; }
     }
     __syncwarp();
   }
+  __syncwarp();
+  if (sm_work)
+    for (int i = lane; i < n; i += 32) w.iperm[i] = iperm[i];
+  if (sm_rows)
+    for (int i = lane; i < n; i += 32) { w.u_dinv64[i] = udinv[i]; w.u_len[i] = ulen_a[i]; w.lev_l[i] = levl[i]; }
+  __syncwarp();
   *npiv_out = npiv;
   *nnz_out = nnz;
   *p_out = p;
   return flags;
+}
+
+// ---------------------------------------------------------------------------
+// Level-ordered chunk stream of one triangular factor, consumed by the staged
+// solve: levels in solve order, each level split greedily into chunks of at most
+// kChunkRows rows and kSlotBytes bytes (the rows of a chunk are independent).
+// Returns the number of chunks.  Block-wide.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ int build_stream(const Walker& w, bool upper, int nlev, Shared& sh) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int* lptr = upper ? w.u_lvl_ptr : w.l_lvl_ptr;
+  const int* rows = upper ? w.u_lvl_rows : w.l_lvl_rows;
+  const int* len = upper ? w.u_len : w.l_len;
+  const int* colv = upper ? w.u_col : w.l_col;
+  const double* valv = upper ? w.u_val64 : w.l_val64;
+  int2* tab = upper ? w.uchunk : w.lchunk;
+  unsigned char* stream = upper ? w.ustream : w.lstream;
+  const int tsz = (int)sizeof(T), capLU = w.capLU;
+  // pass A: chunks per level
+  for (int lev = wid; lev < nlev; lev += nw) {
+    if (lane == 0) {
+      int q = lptr[lev];
+      const int e = lptr[lev + 1];
+      int nch = 0;
+      while (q < e) {
+        int nr = 0, ne = 0;
+        while (q < e && nr < kChunkRows) {
+          const int L = len[rows[q]];
+          if (nr > 0 && chunk_bytes(nr + 1, ne + L, tsz, upper) > kSlotBytes) break;
+          ++nr; ne += L; ++q;
+        }
+        ++nch;
+      }
+      w.lvl_nchunk[lev] = nch;
+    }
+  }
+  __syncthreads();
+  const int nch_total = block_scan_inplace(w.lvl_nchunk, nlev, sh);
+  // pass B: chunk metadata and sizes (same greedy rule)
+  for (int lev = wid; lev < nlev; lev += nw) {
+    if (lane == 0) {
+      int q = lptr[lev];
+      const int e = lptr[lev + 1];
+      int c = w.lvl_nchunk[lev];
+      while (q < e) {
+        const int q0 = q;
+        int nr = 0, ne = 0;
+        while (q < e && nr < kChunkRows) {
+          const int L = len[rows[q]];
+          if (nr > 0 && chunk_bytes(nr + 1, ne + L, tsz, upper) > kSlotBytes) break;
+          ++nr; ne += L; ++q;
+        }
+        w.chunk_meta[c] = make_int4(q0, nr, ne, q == e ? 1 : 0);
+        w.lvl_cur[c] = chunk_bytes(nr, ne, tsz, upper);
+        ++c;
+      }
+    }
+  }
+  __syncthreads();
+  for (int c = tid; c < nch_total; c += nt) tab[c].y = w.lvl_cur[c];
+  __syncthreads();
+  block_scan_inplace(w.lvl_cur, nch_total, sh);
+  for (int c = tid; c < nch_total; c += nt) tab[c].x = w.lvl_cur[c];
+  __syncthreads();
+  // pass C: fill the chunks, one warp per chunk
+  for (int c = wid; c < nch_total; c += nw) {
+    const int4 md = w.chunk_meta[c];
+    const int q0 = md.x, nr = md.y, ne = md.z;
+    unsigned char* base = stream + tab[c].x;
+    int* rws = (int*)(base + kChunkHdr);
+    int* st = rws + pad4(nr);
+    int* cl = st + pad4(nr + 1);
+    T* vl = (T*)(cl + pad4(ne));
+    T* dv = (T*)((unsigned char*)vl + pad16(tsz * ne));
+    if (lane == 0) *(int4*)base = make_int4(nr, ne, md.w, 0);
+    if (lane < kMaxSlots) ((int2*)(base + 16))[lane] = c + 1 + lane < nch_total ? tab[c + 1 + lane] : make_int2(0, 0);
+    int carry = 0;
+    for (int b0 = 0; b0 < nr; b0 += 32) {
+      const int i = b0 + lane;
+      const int r = i < nr ? rows[q0 + i] : 0;
+      const int L = i < nr ? len[r] : 0;
+      int inc = L;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+      }
+      if (i < nr) {
+        rws[i] = r;
+        st[i] = carry + inc - L;
+        if (upper) dv[i] = (T)w.u_dinv64[r];
+      }
+      carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) st[nr] = carry;
+    __syncwarp();
+    for (int i = 0; i < nr; ++i) {
+      const int r = rws[i];
+      const int b = st[i], L = st[i + 1] - b;
+      for (int t = lane; t < L; t += 32) {
+        cl[b + t] = colv[(size_t)r * capLU + t];
+        vl[b + t] = (T)valv[(size_t)r * capLU + t];
+      }
+    }
+  }
+  __syncthreads();
+  return nch_total;
 }
 
 // Block-wide: relabel U columns to factor labels, compute U levels (warp 0,
@@ -350,18 +563,12 @@ __device__ __noinline__ void relabel_and_levels(const Walker& w, Shared& sh) {
   for (int q = tid; q < nlu; q += nt) w.lvl_cur[q] = w.u_lvl_ptr[q];
   __syncthreads();
   for (int r = tid; r < n; r += nt) w.u_lvl_rows[atomicAdd(&w.lvl_cur[w.lev_u[r]], 1)] = r;
-  // working-precision copies of the factors
-  if (sizeof(T) != sizeof(double)) {
-    T* lv = (T*)w.l_valT;
-    T* uv = (T*)w.u_valT;
-    T* dv = (T*)w.u_dinvT;
-    for (int idx = tid; idx < n * capLU; idx += nt) {
-      lv[idx] = (T)w.l_val64[idx];
-      uv[idx] = (T)w.u_val64[idx];
-    }
-    for (int r = tid; r < n; r += nt) dv[r] = (T)w.u_dinv64[r];
-  }
   if (tid == 0) { w.ctl->nlev_l = nll; w.ctl->nlev_u = nlu; }
+  __syncthreads();
+  const int ncl = build_stream<T>(w, false, nll, sh);
+  const int ncu = build_stream<T>(w, true, nlu, sh);
+  if (tid == 0) { w.ctl->nchunk_l = ncl; w.ctl->nchunk_u = ncu; }
+  fence_proxy_async_global();  // the streams are read next by bulk (async-proxy) copies
   __syncthreads();
 }
 
@@ -369,12 +576,19 @@ __device__ __noinline__ void relabel_and_levels(const Walker& w, Shared& sh) {
 // Block-wide.  Returns the ILUTP flags.
 template <typename T>
 __device__ __noinline__ int factor_block(const Walker& w, const Params& P, Shared& sh, bool reorder) {
-  if (reorder) reorder_block(w, sh);
+  const long long t0 = clock64();
+  if (reorder) {
+    reorder_block(w, sh);
+    if (threadIdx.x == 0) w.ctl->cyc[PH_REORDER] += clock64() - t0;
+  }
   if (threadIdx.x < 32) {
     int npiv = 0, p = 0;
     double nnz = 0.0;
     for (int r = threadIdx.x; r < w.n; r += 32) w.lev_u[r] = 0;
-    const int fl = ilutp_warp(w, P, sh, &npiv, &nnz, &p);
+    const long long ti = clock64();
+    const int fl = ilutp_warp<T>(w, P, sh, &npiv, &nnz, &p);
+    if (threadIdx.x == 0) w.ctl->cyc[PH_ILUTP] += clock64() - ti;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // scratch is reused by bulk copies
     if (threadIdx.x == 0) {
       sh.iflag[0] = fl;
       Ctl* c = w.ctl;
@@ -383,16 +597,20 @@ __device__ __noinline__ int factor_block(const Walker& w, const Params& P, Share
       c->p_lfil = p;
       c->factorizations += 1;
       c->n_upd = 0;
+      c->upd_nnz = 0;
       c->last_breakdown = fl & 1;
     }
   }
   __syncthreads();
   const int fl = sh.iflag[0];
+  const long long tl = clock64();
   relabel_and_levels<T>(w, sh);
+  if (threadIdx.x == 0) w.ctl->cyc[PH_LEVELS] += clock64() - tl;
   if (threadIdx.x == 0) {
     long long tot = 0;
     for (int i = 0; i < w.n; ++i) tot += w.a_len[i];
     w.ctl->nnz_A = (double)tot;
+    w.ctl->cyc[PH_FACTOR] += clock64() - t0;
   }
   __syncthreads();
   return fl;

@@ -54,7 +54,7 @@ class vmc_stats(C.Structure):
                 ("refactors_updates", C.c_int64), ("factorizations", C.c_int64), ("pivots", C.c_int64),
                 ("N_max_seen", C.c_double), ("N_sum", C.c_double), ("nnz_A", C.c_double), ("nnz_LU", C.c_double),
                 ("levels_L", C.c_int), ("levels_U", C.c_int), ("n_updates", C.c_int), ("status", C.c_int),
-                ("its_hist", C.c_int64 * 64)]
+                ("its_hist", C.c_int64 * 64), ("phase_cycles", C.c_int64 * 16), ("alg_bytes", C.c_double)]
 
 
 # name -> (restype, argtypes); every symbol the header declares
@@ -201,8 +201,9 @@ def vmc_synchronize(ctx) -> None:
 def vmc_get_stats(ctx, walker: int) -> dict:
     st = vmc_stats()
     _check(lib().vmc_get_stats(ctx, walker, C.byref(st)), ctx)
-    d = {name: getattr(st, name) for name, _ in vmc_stats._fields_ if name != "its_hist"}
+    d = {name: getattr(st, name) for name, _ in vmc_stats._fields_ if name not in ("its_hist", "phase_cycles")}
     d["its_hist"] = list(st.its_hist)
+    d["phase_cycles"] = list(st.phase_cycles)
     return d
 
 
