@@ -187,6 +187,33 @@ vmc_status vmc_refactor(vmc_ctx* ctx, int walker, int reorder);
  * words, out: 4n words): checks the device generator against its definition. */
 vmc_status vmc_philox_device(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n);
 
+/* ---- determinant ratio without device allocation ------------------------------- */
+/* The paper has no counterpart to this entry point; it serves callers that cannot
+ * call cudaMalloc (a framework that owns all device memory through its own pool,
+ * latency-critical code where an allocation's implicit synchronisation is not
+ * acceptable, or a process that has already reserved the free memory).
+ * vmc_ratio_noalloc computes det(A')/det(A) for moving particle k of ONE walker to
+ * r_new, like vmc_create + vmc_set_positions + vmc_ratio with the same parameters,
+ * but allocates nothing: the whole walker workspace lives in a fixed device array of
+ * vmc_noalloc_capacity() bytes (16 MiB) that every GPU loading this library holds
+ * until the process exits.
+ *   sys, params : host; params may be NULL (defaults); engine is ignored.
+ *   xyz_dev     : device, n*3 doubles, positions in [0, K a) in particle order.
+ *   k, r_new    : particle index and its proposed position (host, 3 doubles).
+ *   ratio_dev   : device, one double, receives the ratio.
+ *   stream      : cudaStream_t or NULL; the call synchronises it before returning.
+ * Returns VMC_ERR_CAPACITY when the system's workspace exceeds the fixed array,
+ * VMC_ERR_INVALID for bad arguments, other codes as vmc_ratio; the message is in
+ * vmc_noalloc_last_error() (per host thread).
+ * The array's device address is looked up on the first call made with each device
+ * current; make that first call before any stream capture.  Every call reuses and
+ * overwrites the same array, so calls that overlap on the GPU (other streams,
+ * other host threads) race: serialise them. */
+vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_params* params, const double* xyz_dev,
+                             int k, const double r_new[3], double* ratio_dev, void* stream);
+size_t vmc_noalloc_capacity(void);
+const char* vmc_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,10 @@ _SIG = {
     "vmc_apply_preconditioner": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "vmc_refactor": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "vmc_philox_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "vmc_ratio_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
+    "vmc_noalloc_capacity": (C.c_size_t, []),
+    "vmc_noalloc_last_error": (C.c_char_p, []),
 }
 
 
@@ -258,6 +262,26 @@ def vmc_philox_device(ctr, key) -> np.ndarray:
     out = np.zeros_like(c)
     _check(lib().vmc_philox_device(_p(c), _p(k), _p(out), c.shape[0]))
     return out
+
+
+def vmc_ratio_noalloc(system, params, xyz_dev, k: int, r_new, ratio_dev, stream=None) -> None:
+    """Ratio of one move without device allocation; xyz_dev and ratio_dev are CUDA
+    tensors (float64, n*3 and 1 element) owned by the caller."""
+    K, lat, a, kap, rc = system
+    sysc = vmc_system(int(K), int(lat), float(a), float(kap), float(rc))
+    r = np.ascontiguousarray(r_new, dtype=np.float64)
+    st = lib().vmc_ratio_noalloc(C.byref(sysc), C.byref(params) if params is not None else None, _p(xyz_dev), k,
+                                 _p(r), _p(ratio_dev), _stream_handle(stream))
+    if st != 0:
+        raise VmcError(st, lib().vmc_noalloc_last_error().decode(errors="replace"))
+
+
+def vmc_noalloc_capacity() -> int:
+    return lib().vmc_noalloc_capacity()
+
+
+def vmc_noalloc_last_error() -> str:
+    return lib().vmc_noalloc_last_error().decode(errors="replace")
 
 
 def params(**kw) -> vmc_solver_params:
