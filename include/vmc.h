@@ -113,6 +113,9 @@ typedef struct {
                                 triangular-factor chunks (inside 7), 15 unused */
   double alg_bytes;          /* algorithmic (compulsory) bytes of the solves: per phase the
                                 matrix/factor values and indices, the vectors read and written */
+  int64_t ilu_rows, ilu_elims, ilu_cand; /* ILUTP rows factored, eliminations performed, and
+                                working-row entries before dropping (summed over rows) */
+  int chunks_L, chunks_U;    /* stream chunks of the triangular solves (>= levels)         */
 } vmc_stats;
 
 /* Fill p with the defaults above. */
@@ -183,6 +186,14 @@ vmc_status vmc_get_factors(vmc_ctx* ctx, int walker, double* L_dense, double* U_
 vmc_status vmc_apply_preconditioner(vmc_ctx* ctx, int walker, const double* v, double* z);
 /* Force a reorder + refactorisation of walker w now (tests). */
 vmc_status vmc_refactor(vmc_ctx* ctx, int walker, int reorder);
+/* Kernel microbenchmark over all walkers (no synchronisation; the caller times the
+ * launch on the context's stream): `reps` back-to-back applications of one hot-path
+ * kernel per walker -- which = 0: the L and U level-scheduled triangular solves
+ * (Sec. 3.2 Eq. 18 without the update chain), 1: the SpMV y = A_p x in the working
+ * precision, 2: the whole preconditioner apply -- on a fixed vector.  The walkers'
+ * alg_bytes statistic grows by the algorithmic bytes moved.  Clobbers the walkers'
+ * Krylov work vectors (any pending vmc_ratio is dropped). */
+vmc_status vmc_kernel_bench(vmc_ctx* ctx, int which, int reps);
 /* Philox4x32-10 on the device for n counters (host arrays ctr: 4n words, key: 2
  * words, out: 4n words): checks the device generator against its definition. */
 vmc_status vmc_philox_device(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n);

@@ -78,6 +78,7 @@ def lib():
                 "orc_chains": (C.c_long, [sp, i, p, d, i, i, C.c_long, i, i, p, p, p, i]),
                 "orc_max_threads": (i, []),
                 "orc_kinetic_energy": (d, [sp, p, p]),
+                "orc_greedy_pairing": (None, [sp, p, p, p, p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -274,6 +275,15 @@ def chains(s: System, seeds, sigma: float, R0: np.ndarray, n_sweeps: int, first_
 
 def max_threads() -> int:
     return lib().orc_max_threads()
+
+
+def greedy_pairing(s: System, R: np.ndarray, Z: np.ndarray, P, Q):
+    """The greedy particle/orbital reordering of Sec. 3.1; returns the new (P, Q)."""
+    PP = np.ascontiguousarray(P, dtype=np.int32).copy()
+    QQ = np.ascontiguousarray(Q, dtype=np.int32).copy()
+    lib().orc_greedy_pairing(C.byref(s), _ptr(np.ascontiguousarray(R)), _ptr(np.ascontiguousarray(Z)),
+                             _ptr(PP), _ptr(QQ))
+    return PP, QQ
 
 
 def kinetic_energy(s: System, Z: np.ndarray, R: np.ndarray) -> float:

@@ -622,6 +622,40 @@ int orc_max_threads(void) {
 }
 
 /* ======================================================================== */
+/* Geometric reordering, Sec. 3.1: the greedy particle/orbital rule.         */
+/* ======================================================================== */
+static double pair_dist2(const orc_system* s, const double* r, const double* z) {
+  double L = box_len(s);
+  double dx = min_image(r[0] - z[0], L);
+  double dy = min_image(r[1] - z[1], L);
+  double dz = min_image(r[2] - z[2], L);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+void orc_greedy_pairing(const orc_system* s, const double* R, const double* Z, int* P, int* Q) {
+  int n = orc_n(s);
+  for (int i = 0; i < n - 1; ++i) {
+    int bj = i;
+    double bd = pair_dist2(s, R + 3 * P[i], Z + 3 * Q[i]);
+    for (int j = i + 1; j < n; ++j) {
+      double d = pair_dist2(s, R + 3 * P[i], Z + 3 * Q[j]);
+      if (d < bd) { bd = d; bj = j; }
+    }
+    if (bj != i) {
+      int t = Q[i]; Q[i] = Q[bj]; Q[bj] = t;
+    } else {
+      int bk = i;
+      double bdk = pair_dist2(s, R + 3 * P[i], Z + 3 * Q[i]);
+      for (int k = i + 1; k < n; ++k) {
+        double d = pair_dist2(s, R + 3 * P[k], Z + 3 * Q[i]);
+        if (d < bdk) { bdk = d; bk = k; }
+      }
+      if (bk != i) { int t = P[i]; P[i] = P[bk]; P[bk] = t; }
+    }
+  }
+}
+
+/* ======================================================================== */
 /* Kinetic energy, Eq. 21 with hbar = mass = 1.  -1/2 lap phi = (3k - 2k^2   */
 /* d^2) phi for phi = exp(-k d^2), so the estimator is                       */
 /*   (1/2n) sum_{p,o} (6k - 4k^2 |r_p - Z_o|^2) A_po (A^{-1})_op.            */

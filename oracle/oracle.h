@@ -105,6 +105,14 @@ long orc_chains(const orc_system* s, int n_walkers, const uint64_t* seeds, doubl
                 uint8_t* accept_log, int threads);
 int orc_max_threads(void);
 
+/* ---- geometric reordering (Sec. 3.1, the greedy rule) -------------------------- */
+/* P[i] = particle at position i, Q[i] = orbital at position i (in/out).  For
+ * i = 0..n-2: the orbital nearest to particle P[i] among positions >= i is swapped into
+ * position i; if that is already position i, the particle nearest to orbital Q[i] among
+ * positions >= i is swapped into position i.  Minimum-image distances, ties to the
+ * lowest position. */
+void orc_greedy_pairing(const orc_system* s, const double* R, const double* Z, int* P, int* Q);
+
 /* ---- kinetic energy (Eq. 21): (1/2n) sum_{p,o} (6k - 4k^2 |r_p - Z_o|^2) A_po (A^-1)_op */
 double orc_kinetic_energy(const orc_system* s, const double* Z, const double* R);
 

@@ -20,6 +20,22 @@ using namespace vmc;
 // ---------------------------------------------------------------------------
 namespace vmc {
 
+void plan_smem(int ybytes, int budget, Params& P) {
+  int avail = budget;
+  if (ybytes + 2 * kSlotBytes <= budget) {
+    P.y_smem = 1;
+    P.y_bytes = ybytes;
+    avail = budget - ybytes;
+  } else {
+    P.y_smem = 0;
+    P.y_bytes = 0;
+  }
+  P.slot_bytes = avail >= 4 * 2 * kSlotBytes ? 2 * kSlotBytes : kSlotBytes;
+  P.ring_slots = std::min(kMaxSlots, avail / P.slot_bytes);
+  // the rest of the budget is ILUTP scratch (work row, U-row cache)
+  P.dsm_bytes = std::max(budget, P.y_bytes + P.ring_slots * P.slot_bytes);
+}
+
 static int count_sites_within(int lattice, double a, double gx, double gy, double gz, double R) {
   const int per = lattice == 1 ? 2 : 1;
   int cnt = 0;
@@ -82,7 +98,7 @@ int make_layout(int K, int lattice, double a, double r_c, Layout& out, const cha
   for (int z = 0; z <= G; ++z)
     for (int y = 0; y <= G; ++y)
       for (int x = 0; x <= G; ++x) mx = std::max(mx, count_sites_within(lattice, a, x * h, y * h, z * h, R));
-  out.cap = std::min(n, (mx + 3) / 4 * 4);
+  out.cap = (std::min(n, mx) + 3) / 4 * 4;  // multiple of 4: 16-byte slot loads stay in the slot
   if (out.cap > kMaxRow) { *why = "r_c too large: a Slater row could exceed 256 orbitals"; return 1; }
   return 0;
 }
@@ -307,18 +323,8 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     const int budget2 = per_sm / 2 - 1024 - stat;
     int budget = budget1;
     if (n_walkers > nsm && budget2 >= ybytes + 2 * kSlotBytes) budget = budget2;
-    if (ybytes + 2 * kSlotBytes <= budget) {
-      ctx->P.y_smem = 1;
-      ctx->P.y_bytes = ybytes;
-      ctx->P.ring_slots = std::min(kMaxSlots, (budget - ybytes) / kSlotBytes);
-    } else {
-      ctx->P.y_smem = 0;
-      ctx->P.y_bytes = 0;
-      ctx->P.ring_slots = std::min(kMaxSlots, budget / kSlotBytes);
-    }
-    // the rest of the budget is ILUTP scratch (work row, U-row cache)
-    ctx->smem = (size_t)std::max(budget, ctx->P.y_bytes + ctx->P.ring_slots * kSlotBytes);
-    ctx->P.dsm_bytes = (int)ctx->smem;
+    plan_smem(ybytes, budget, ctx->P);
+    ctx->smem = (size_t)ctx->P.dsm_bytes;
   }
   const size_t ctl_off = cv.take<Ctl>(n_walkers);
   const size_t walk_off = cv.take<Walker>(n_walkers);
@@ -598,6 +604,11 @@ extern "C" vmc_status vmc_get_stats(vmc_ctx* ctx, int walker, vmc_stats* out) {
   for (int b = 0; b < kHistBins; ++b) out->its_hist[b] = h.hist[b];
   for (int b = 0; b < 16; ++b) out->phase_cycles[b] = h.cyc[b];
   out->alg_bytes = h.alg_bytes;
+  out->ilu_rows = h.ilu_rows;
+  out->ilu_elims = h.ilu_elims;
+  out->ilu_cand = h.ilu_cand;
+  out->chunks_L = h.nchunk_l;
+  out->chunks_U = h.nchunk_u;
   return VMC_OK;
 }
 
@@ -614,6 +625,7 @@ extern "C" vmc_status vmc_reset_stats(vmc_ctx* ctx) {
     for (long long& b : c.hist) b = 0;
     for (long long& b : c.cyc) b = 0;
     c.alg_bytes = 0.0;
+    c.ilu_rows = c.ilu_elims = c.ilu_cand = 0;
   }
   CK(cudaMemcpyAsync(ctx->dCtl, h.data(), sizeof(Ctl) * ctx->nw, cudaMemcpyHostToDevice, ctx->stream), "stats");
   CK(cudaStreamSynchronize(ctx->stream), "synchronize");
@@ -701,6 +713,14 @@ extern "C" vmc_status vmc_refactor(vmc_ctx* ctx, int walker, int reorder) {
   CK(launch_refactor(cfg(ctx), ctx->dW, walker, ctx->P, reorder), "refactor kernel");
   ctx->pending[walker] = 0;
   return check_walker_status(ctx);
+}
+
+extern "C" vmc_status vmc_kernel_bench(vmc_ctx* ctx, int which, int reps) {
+  if (!ctx || which < 0 || which > 2 || reps < 1) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  if (!ctx->ready) return fail(ctx, VMC_ERR_STATE, "positions not set");
+  CK(launch_bench(cfg(ctx), ctx->dW, ctx->nw, ctx->P, which, reps), "bench kernel");
+  for (int w = 0; w < ctx->nw; ++w) ctx->pending[w] = 0;
+  return VMC_OK;
 }
 
 extern "C" vmc_status vmc_philox_device(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n) {

@@ -30,7 +30,7 @@ constexpr int kMaxRowNZ = 2048;   // ILUTP working-row entries before dropping
 constexpr int kMaxSel = 1024;     // ILUTP candidates of one triangle
 constexpr int kMaxUpd = 128;      // longest preconditioner update chain
 constexpr int kHistBins = 64;
-constexpr int kSlotBytes = 8192;  // one shared-memory ring slot = largest stream chunk
+constexpr int kSlotBytes = 8192;  // smallest ring slot (a slot holds the largest stream chunk)
 constexpr int kMaxSlots = 8;      // ring depth (chunks in flight)
 constexpr int kChunkRows = 256;   // rows per chunk at most
 constexpr int kChunkHdr = 80;     // chunk header bytes: int4 + 8 next-chunk descriptors
@@ -66,6 +66,7 @@ struct Ctl {
   long long hist[kHistBins];
   long long cyc[16];  // clock64 cycles by phase (see vmc_stats.phase_cycles)
   double alg_bytes;   // compulsory (algorithmic) bytes moved by the solves, counted per phase
+  long long ilu_rows, ilu_elims, ilu_cand;  // ILUTP rows, eliminations, working-row entries
   int upd_nnz;        // total nonzeros of the u vectors in the update chain
 };
 
@@ -108,6 +109,7 @@ struct Params {
   int ring_slots;   // shared-memory ring depth for the triangular-solve streams
   int y_smem;       // 1: the triangular-solve vector lives in shared memory
   int y_bytes;      // bytes reserved for it (multiple of 128)
+  int slot_bytes;   // bytes of one ring slot = largest stream chunk (multiple of 16)
   int dsm_bytes;    // total dynamic shared memory (ILUTP scratch may use all of it)
 };
 
@@ -125,6 +127,9 @@ struct __align__(16) Shared {
       int nz[kMaxRowNZ];
       int selF[kMaxSel];
       double selV[kMaxSel];
+      unsigned char selK[kMaxSel];    // top-k selection result per candidate
+      int hist[64];                   // exponent histogram of the selection
+      int bndE[256];                  // candidates of the boundary octave
     };
   };
   double red[40];
@@ -151,6 +156,9 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
 }
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
@@ -185,7 +193,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // Byte layout of one stream chunk (all offsets multiples of 16):
-//   int4 header {rows, entries, level_end, 0}; int2 next[8] (descriptors {offset, bytes}
+//   int4 header {rows, entries, level_end, log2 of the lane-group size}; int2 next[8]
+//   (descriptors {offset, bytes}
 //   of the following 8 chunks, {0, 0} past the end); int rows[pad4(r)]; int starts[pad4(r+1)];
 //   int cols[pad4(e)]; T vals[e] (padded to 16 B); U only: T dinv[r] (padded).
 __host__ __device__ __forceinline__ int pad4(int x) { return (x + 3) & ~3; }

@@ -339,6 +339,39 @@ __global__ void __launch_bounds__(kMaxThreads) k_apply_precond(const Walker* __r
   for (int i = threadIdx.x; i < w.n; i += blockDim.x) w.x64[i] = (double)Zk[i];
 }
 
+// Microbenchmark: `reps` back-to-back applications of one hot-path kernel per walker
+// (0: L and U triangular solves, 1: SpMV in the working precision, 2: the full
+// preconditioner apply with the update chain), on V[0] = 1 / sqrt(n).
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) k_bench(const Walker* __restrict__ W, Params P, int which, int reps) {
+  __shared__ Shared sh;
+  ring_init(sh, P);
+  const Walker& w = W[blockIdx.x];
+  const int n = w.n;
+  T* V = (T*)w.V;
+  T* Zk = (T*)w.Zk;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) V[i] = (T)rsqrt((double)n);
+  __syncthreads();
+  T* y = P.y_smem ? (T*)dyn_smem() : (T*)w.tv;
+  for (int it = 0; it < reps; ++it) {
+    if (which == 0) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = V[i];
+      __syncthreads();
+      tri_staged<T>(w, P, false, y, sh);
+      tri_staged<T>(w, P, true, y, sh);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) Zk[w.perm[i]] = y[i];
+      if (threadIdx.x == 0)
+        w.ctl->alg_bytes += w.ctl->nnz_LU * (sizeof(T) + 4) + (double)n * (3 * sizeof(T) + 8);
+    } else if (which == 1) {
+      spmv<T>(w, V, Zk);
+      if (threadIdx.x == 0) w.ctl->alg_bytes += w.ctl->nnz_A * (sizeof(T) + 4) + (double)n * (2 * sizeof(T) + 4);
+    } else {
+      precond_apply<T>(w, P, V, Zk, sh);
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -406,6 +439,10 @@ cudaError_t launch_refactor(const LaunchCfg& L, const Walker* W, int wi, const P
 cudaError_t launch_apply_precond(const LaunchCfg& L, const Walker* W, int wi, const Params& P) {
   if (L.fp64) VMC_LAUNCH(k_apply_precond<double>, 1, W, wi, P);
   VMC_LAUNCH(k_apply_precond<float>, 1, W, wi, P);
+}
+cudaError_t launch_bench(const LaunchCfg& L, const Walker* W, int nwalk, const Params& P, int which, int reps) {
+  if (L.fp64) VMC_LAUNCH(k_bench<double>, nwalk, W, P, which, reps);
+  VMC_LAUNCH(k_bench<float>, nwalk, W, P, which, reps);
 }
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, cudaStream_t s) {
   k_philox<<<(n + 127) / 128, 128, 0, s>>>(ctr, key, out, n);

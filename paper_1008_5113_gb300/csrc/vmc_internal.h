@@ -30,9 +30,15 @@ cudaError_t launch_init_positions(const LaunchCfg& L, const Walker* W, int nwalk
 cudaError_t launch_setup(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P);
 cudaError_t launch_refactor(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int reorder);
 cudaError_t launch_apply_precond(const LaunchCfg& L, const Walker* W, int wi, const Params& P);
+cudaError_t launch_bench(const LaunchCfg& L, const Walker* W, int nwalk, const Params& P, int which, int reps);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, cudaStream_t s);
 
-// host-side geometry and layout (vmc_layout.cpp)
+// Shared-memory plan of a walker CTA: the solve vector (ybytes) in shared memory when
+// it fits next to a ring of >= 2 slots; 16 KB slots when at least four fit, else 8 KB.
+// Fills y_smem, y_bytes, ring_slots, slot_bytes, dsm_bytes.
+void plan_smem(int ybytes, int budget, Params& P);
+
+// host-side geometry and layout
 struct Layout {
   int n, per, cap;
   std::vector<double> Z;       // n*3

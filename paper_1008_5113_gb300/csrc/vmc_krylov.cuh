@@ -22,19 +22,59 @@ __device__ __forceinline__ const float* a_vals<float>(const Walker& w) { return 
 template <>
 __device__ __forceinline__ const double* a_vals<double>(const Walker& w) { return w.a_val; }
 
-// y = A_p x (thread per row; rows gathered through the particle slot of each row)
+// 16-byte vector views of the Slater slots (slot starts are 16-byte aligned: cap % 4 == 0)
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+  float v[4];
+  __device__ __forceinline__ void load(const float* p) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+};
+template <> struct Vec4<double> {
+  double v[4];
+  __device__ __forceinline__ void load(const double* p) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+};
+
+// Dot product of Slater slot p (len entries) with x: 16-byte loads of four column
+// indices and four values at a time; entries past len are masked (slots hold valid
+// column indices there, so the gathers stay in bounds).
+template <typename T, typename X>
+__device__ __forceinline__ X slot_dot(const int* __restrict__ cols, const T* __restrict__ vals, int len,
+                                      const X* __restrict__ x) {
+  X acc = 0;
+  for (int q = 0; q < len; q += 4) {
+    const int4 c = *reinterpret_cast<const int4*>(cols + q);
+    Vec4<T> v;
+    v.load(vals + q);
+    const X x0 = x[c.x], x1 = x[c.y], x2 = x[c.z], x3 = x[c.w];
+    acc += (X)v.v[0] * x0;
+    if (q + 1 < len) acc += (X)v.v[1] * x1;
+    if (q + 2 < len) acc += (X)v.v[2] * x2;
+    if (q + 3 < len) acc += (X)v.v[3] * x3;
+  }
+  return acc;
+}
+
+// y = A_p x, one row per thread; the next row's slot and length are fetched while
+// the current row is summed.
 template <typename T>
 __device__ __forceinline__ void spmv(const Walker& w, const T* __restrict__ x, T* __restrict__ y) {
   const T* av = a_vals<T>(w);
-  const int n = w.n, cap = w.cap;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    const int p = w.part_of_row[r];
-    const int len = w.a_len[p];
-    const int* c = w.a_col + (size_t)p * cap;
-    const T* v = av + (size_t)p * cap;
-    T acc = 0;
-    for (int t = 0; t < len; ++t) acc += v[t] * x[c[t]];
-    y[r] = acc;
+  const int n = w.n, cap = w.cap, nt = blockDim.x;
+  int r = threadIdx.x;
+  int p = r < n ? w.part_of_row[r] : 0;
+  int len = r < n ? w.a_len[p] : 0;
+  for (; r < n; r += nt) {
+    const int rn = r + nt;
+    const int pn = rn < n ? w.part_of_row[rn] : 0;
+    y[r] = slot_dot<T, T>(w.a_col + (size_t)p * cap, av + (size_t)p * cap, len, x);
+    len = rn < n ? w.a_len[pn] : 0;
+    p = pn;
   }
 }
 
@@ -53,55 +93,57 @@ __device__ __forceinline__ void ring_init(Shared& sh, const Params& P) {
 // One triangular solve in place on y (shared or global), streaming the factor's
 // chunks through the ring with bulk copies issued ring_slots chunks ahead.
 // Lower: y_r -= sum_t L_rt y_t.  Upper: y_r = (y_r - sum_t U_rt y_t) / U_rr.
+// Each chunk is one level (or part of one): its rows are independent, solved by
+// lane groups of 2^gs lanes (gs stored in the chunk header); one barrier per chunk.
 template <typename T>
 __device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, bool upper, T* y, Shared& sh) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x;
   const unsigned char* stream = upper ? w.ustream : w.lstream;
   const int2* tab = upper ? w.uchunk : w.lchunk;
   const int nch = upper ? w.ctl->nchunk_u : w.ctl->nchunk_l;
   const int S = P.ring_slots;
+  const int SB = P.slot_bytes;
   unsigned char* ring = dyn_smem() + P.y_bytes;
   const int seq0 = sh.ring_seq;
+  long long twait = 0;
+  int slot = seq0 % S;
+  unsigned parity = (unsigned)((seq0 / S) & 1);
   if (tid == 0) {
     const int pre = min(S, nch);
+    int sl = slot;
     for (int c = 0; c < pre; ++c) {
-      const int slot = (seq0 + c) % S;
       const int2 tc = tab[c];
-      mbar_expect_tx(&sh.bar[slot], (unsigned)tc.y);
-      bulk_g2s(ring + (size_t)slot * kSlotBytes, stream + tc.x, (unsigned)tc.y, &sh.bar[slot]);
+      mbar_expect_tx(&sh.bar[sl], (unsigned)tc.y);
+      bulk_g2s(ring + (size_t)sl * SB, stream + tc.x, (unsigned)tc.y, &sh.bar[sl]);
+      if (++sl == S) sl = 0;
     }
   }
   for (int c = 0; c < nch; ++c) {
-    const int g = seq0 + c;
-    const int slot = g % S;
     const long long tw = clock64();
-    if (!mbar_wait(&sh.bar[slot], (unsigned)((g / S) & 1))) sh.iflag[3] = 1;
-    if (tid == 0) w.ctl->cyc[PH_TRIWAIT] += clock64() - tw;
-    const unsigned char* ch = ring + (size_t)slot * kSlotBytes;
+    if (!mbar_wait(&sh.bar[slot], parity)) sh.iflag[3] = 1;
+    twait += clock64() - tw;
+    const unsigned char* ch = ring + (size_t)slot * SB;
     const int4 hd = *(const int4*)ch;
-    const int nr = hd.x, ne = hd.y;
+    const int nr = hd.x, ne = hd.y, gs = hd.w;
     const int* rws = (const int*)(ch + kChunkHdr);
     const int* st = rws + pad4(nr);
     const int* cl = st + pad4(nr + 1);
     const T* vl = (const T*)(cl + pad4(ne));
     const T* dv = (const T*)((const unsigned char*)vl + pad16((int)sizeof(T) * ne));
-    // G lanes per row (G a power of two, as large as the chunk's row count allows),
-    // each lane a strided slice of the row, then a G-lane shuffle reduction
-    int G = 1;
-    while (G < 32 && (G << 1) * nr <= nt) G <<= 1;
-    const int gid = tid / G, gl = tid & (G - 1), ng = nt / G;
-    for (int base = 0; base < nr; base += ng) {
-      const int i = base + gid;
-      const bool valid = i < nr;
+    const int G = 1 << gs;
+    const int gl = tid & (G - 1);
+    const int ng = (int)(blockDim.x >> gs);
+    for (int base = 0; base < nr; base += ng) {  // same trip count in every lane
+      const int i = base + (tid >> gs);
       T part = 0;
       int r = 0;
-      if (valid) {
+      if (i < nr) {
         r = rws[i];
         const int e = st[i + 1];
         for (int t = st[i] + gl; t < e; t += G) part += vl[t] * y[cl[t]];
       }
-      for (int o = G >> 1; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      if (valid && gl == 0) {
+      for (int o = G >> 1; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o, G);
+      if (i < nr && gl == 0) {
         T acc = y[r] - part;
         if (upper) acc *= dv[i];
         y[r] = acc;
@@ -112,10 +154,14 @@ __device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, boo
     __syncthreads();
     if (tid == 0 && c + S < nch) {
       mbar_expect_tx(&sh.bar[slot], (unsigned)nx.y);
-      bulk_g2s(ring + (size_t)slot * kSlotBytes, stream + nx.x, (unsigned)nx.y, &sh.bar[slot]);
+      bulk_g2s(ring + (size_t)slot * SB, stream + nx.x, (unsigned)nx.y, &sh.bar[slot]);
     }
+    if (++slot == S) { slot = 0; parity ^= 1u; }
   }
-  if (tid == 0) sh.ring_seq = seq0 + nch;
+  if (tid == 0) {
+    sh.ring_seq = seq0 + nch;
+    w.ctl->cyc[PH_TRIWAIT] += twait;
+  }
   __syncthreads();
 }
 
@@ -155,7 +201,7 @@ __device__ __noinline__ void precond_apply(const Walker& w, const Params& P, con
     }
     // G[0..mu)[0..mu) staged in the (now idle) stream ring when it fits, then
     // c_s = d_s - sum_{t<s} G[s][t] c_t by warp 0
-    const bool gs_smem = (size_t)mu * mu * sizeof(double) <= (size_t)P.ring_slots * kSlotBytes;
+    const bool gs_smem = (size_t)mu * mu * sizeof(double) <= (size_t)P.ring_slots * P.slot_bytes;
     double* Gs = gs_smem ? (double*)(dyn_smem() + P.y_bytes) : w.upd_G;
     const int gld = gs_smem ? mu : kMaxUpd;
     if (gs_smem) {
@@ -313,21 +359,23 @@ __device__ __noinline__ int gmres_inner(const Walker& w, const Params& P, double
 // r64 = e_brow - A_p x64 (FP64); returns ||r64||_2 and, in *xnorm, ||x64||_2.
 // Ends synchronised.
 __device__ __forceinline__ double residual64(const Walker& w, int brow, double* xnorm, Shared& sh) {
-  const int n = w.n, cap = w.cap;
+  const int n = w.n, cap = w.cap, nt = blockDim.x;
   const long long t0 = clock64();
   double ss = 0.0, xx = 0.0;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    const int p = w.part_of_row[r];
-    const int len = w.a_len[p];
-    const int* c = w.a_col + (size_t)p * cap;
-    const double* v = w.a_val + (size_t)p * cap;
-    double acc = 0.0;
-    for (int t = 0; t < len; ++t) acc = fma(v[t], w.x64[c[t]], acc);
+  int r = threadIdx.x;
+  int p = r < n ? w.part_of_row[r] : 0;
+  int len = r < n ? w.a_len[p] : 0;
+  for (; r < n; r += nt) {
+    const int rn = r + nt;
+    const int pn = rn < n ? w.part_of_row[rn] : 0;
+    const double acc = slot_dot<double, double>(w.a_col + (size_t)p * cap, w.a_val + (size_t)p * cap, len, w.x64);
     const double rr = (r == brow ? 1.0 : 0.0) - acc;
     w.r64[r] = rr;
     ss += rr * rr;
     const double xr = w.x64[r];
     xx += xr * xr;
+    len = rn < n ? w.a_len[pn] : 0;
+    p = pn;
   }
   *xnorm = sqrt(block_sum(xx, sh));
   const double rn = sqrt(block_sum(ss, sh));

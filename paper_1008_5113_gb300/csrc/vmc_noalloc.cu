@@ -182,13 +182,8 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   if (optin <= 0 || stat <= 0) return fail(VMC_ERR_CUDA, "no usable CUDA device");
   const int ybytes = (int)(((size_t)n * Tsz + 127) / 128 * 128);
   const int budget = optin - stat;
-  if (ybytes + 2 * kSlotBytes <= budget) {
-    P.y_smem = 1; P.y_bytes = ybytes; P.ring_slots = std::min(kMaxSlots, (budget - ybytes) / kSlotBytes);
-  } else {
-    P.y_smem = 0; P.y_bytes = 0; P.ring_slots = std::min(kMaxSlots, budget / kSlotBytes);
-  }
-  P.dsm_bytes = budget;
-  const LaunchCfg L{s, p.block_threads ? p.block_threads : 256, fp64, (size_t)budget};
+  plan_smem(ybytes, budget, P);
+  const LaunchCfg L{s, p.block_threads ? p.block_threads : 256, fp64, (size_t)P.dsm_bytes};
 
   // clear the part of the scratch this call uses, then fill the inputs
   e = cudaMemsetAsync(base, 0, used, s);

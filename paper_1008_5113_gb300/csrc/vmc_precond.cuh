@@ -60,23 +60,104 @@ __device__ __noinline__ void reorder_block(const Walker& w, Shared& sh) {
   __syncthreads();
 }
 
-// Rank-based top-k of the compacted candidates sh.selF/selV[0..c): keep[e] = rank < keep.
-// Larger magnitude first, ties to the smaller label.
-__device__ __forceinline__ bool sel_keep(const Shared& sh, int c, int e, int keep) {
-  if (c <= keep) return true;
-  const double me = fabs(sh.selV[e]);
-  const int fe = sh.selF[e];
-  int rank = 0;
-  for (int o = 0; o < c; ++o) {
-    const double mo = fabs(sh.selV[o]);
-    rank += (mo > me) || (mo == me && sh.selF[o] < fe);
+// Top-k of the compacted candidates sh.selF/selV[0..c) by magnitude (ties: smaller
+// label), by one warp: a histogram of binary exponents below the largest one (bins
+// of one octave, the last bin collecting everything smaller) finds the octave that
+// holds the k-th largest; entries in higher octaves are kept, entries in that octave
+// are ranked among themselves.  Result in sh.selK[0..c).
+template <typename W>
+__device__ __forceinline__ int octave_bin(W v, int emax) {
+  int e;
+  frexp(v, &e);
+  return min(63, max(0, emax - e));
+}
+template <typename W>
+__device__ void select_topk(Shared& sh, int c, int keep) {
+  const int lane = threadIdx.x & 31;
+  const W* sv = reinterpret_cast<const W*>(sh.selV);
+  if (c <= keep) {
+    for (int e = lane; e < c; e += 32) sh.selK[e] = 1;
+    __syncwarp();
+    return;
   }
-  return rank < keep;
+  W vmax = 0;
+  for (int e = lane; e < c; e += 32) vmax = fmax(vmax, fabs(sv[e]));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  int emax;
+  frexp(vmax, &emax);
+  for (int b = lane; b < 64; b += 32) sh.hist[b] = 0;
+  __syncwarp();
+  for (int e = lane; e < c; e += 32) atomicAdd(&sh.hist[octave_bin<W>(fabs(sv[e]), emax)], 1);
+  __syncwarp();
+  // boundary bin bb: count(bins < bb) < keep <= count(bins <= bb)
+  int h0 = sh.hist[lane], h1 = sh.hist[lane + 32];
+  int inc0 = h0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) { const int v = __shfl_up_sync(0xffffffffu, inc0, o); if (lane >= o) inc0 += v; }
+  const int tot0 = __shfl_sync(0xffffffffu, inc0, 31);
+  int inc1 = h1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) { const int v = __shfl_up_sync(0xffffffffu, inc1, o); if (lane >= o) inc1 += v; }
+  inc1 += tot0;
+  const unsigned m0 = __ballot_sync(0xffffffffu, inc0 >= keep);
+  const unsigned m1 = __ballot_sync(0xffffffffu, inc1 >= keep);
+  const int bb = m0 ? __ffs(m0) - 1 : 32 + __ffs(m1) - 1;
+  const int below = (bb < 32 ? __shfl_sync(0xffffffffu, inc0 - h0, bb & 31)
+                             : __shfl_sync(0xffffffffu, inc1 - h1, bb & 31));
+  const int need = keep - below;  // entries to keep from the boundary bin
+  // compact the boundary octave, decide the others
+  int cb = 0;
+  for (int base = 0; base < c; base += 32) {
+    const int e = base + lane;
+    int b = 64;
+    if (e < c) {
+      b = octave_bin<W>(fabs(sv[e]), emax);
+      sh.selK[e] = b < bb ? 1 : 0;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, b == bb);
+    const int slot = cb + __popc(m & lanemask_lt());
+    if (b == bb && slot < 256) sh.bndE[slot] = e;
+    cb += __popc(m);
+  }
+  __syncwarp();
+  if (cb <= 256) {
+    for (int q = lane; q < cb; q += 32) {
+      const int e = sh.bndE[q];
+      const W me = fabs(sv[e]);
+      const int fe = sh.selF[e];
+      int rank = 0;
+      for (int o = 0; o < cb; ++o) {
+        const int eo = sh.bndE[o];
+        const W mo = fabs(sv[eo]);
+        rank += (mo > me) || (mo == me && sh.selF[eo] < fe);
+      }
+      sh.selK[e] = rank < need ? 1 : 0;
+    }
+  } else {
+    for (int e = lane; e < c; e += 32) {
+      const W me = fabs(sv[e]);
+      if (octave_bin<W>(me, emax) != bb) continue;
+      const int fe = sh.selF[e];
+      int rank = 0;
+      for (int o = 0; o < c; ++o) {
+        const W mo = fabs(sv[o]);
+        if (octave_bin<W>(mo, emax) != bb) continue;
+        rank += (mo > me) || (mo == me && sh.selF[o] < fe);
+      }
+      sh.selK[e] = rank < need ? 1 : 0;
+    }
+  }
+  __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
 // ILUTP, performed by warp 0 of the CTA (rows are sequential); the caller
-// synchronises the block afterwards.  U rows are stored with ORIGINAL column
+// synchronises the block afterwards.  The working row, multipliers, drop and pivot
+// tests run in the engine's working precision T (FP64 engine: FP64; mixed engine:
+// FP32, the precision its factors are stored and applied in -- a warp-serial FP64
+// elimination step costs ~1000 cycles on GB300, whose FP64 rate is 1/48 of FP32);
+// row norms are accumulated in FP64.  U rows are stored with ORIGINAL column
 // labels while the factorisation runs (later pivots relabel columns >= i only)
 // and relabelled to factor labels by relabel_and_levels().
 // Returns: bit 0 breakdown (zero pivot replaced by (1e-4 + tau) ||a_i||), bit 1
@@ -91,24 +172,26 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
   // U lengths and L levels.  Otherwise the global copies are used.
   const size_t dbytes = (size_t)P.dsm_bytes;
   unsigned char* dsm = dyn_smem();
-  double* wrow = w.wrow;
+  T* wrow = reinterpret_cast<T*>(w.wrow);
   int* wpos = w.wpos;
   int* iperm = w.iperm;
-  double* udinv = w.u_dinv64;
+  T* udinv = reinterpret_cast<T*>(w.u_dinv64);
   int* ulen_a = w.u_len;
   int* levl = w.lev_l;
   const bool sm_work = (size_t)16 * n <= dbytes;
   const bool sm_rows = (size_t)32 * n <= dbytes;
   if (sm_work) {
-    wrow = (double*)dsm;
-    wpos = (int*)(wrow + n);
+    wrow = (T*)dsm;
+    wpos = (int*)(dsm + (size_t)8 * n);
     iperm = wpos + n;
   }
   if (sm_rows) {
-    udinv = (double*)(dsm + (size_t)16 * n);
-    ulen_a = (int*)(udinv + n);
+    udinv = (T*)(dsm + (size_t)16 * n);
+    ulen_a = (int*)(dsm + (size_t)24 * n);
     levl = ulen_a + n;
   }
+  // without shared memory the U diagonal lives in the global FP64 array as T values;
+  // it is rewritten as FP64 inverses at the end
   // Cache of finished U rows (original labels; values in the working precision):
   // row r at ucc/ucv[uoff[r] .. uoff[r] + len), uoff[r] = -1 when not cached.
   int* uoff = nullptr;
@@ -149,10 +232,11 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
   p = min(p, (capLU - 2) / 2);
   const int pk = max(0, min(p, capLU - 2 - cap));  // never exceeds the row capacity
   for (int i = lane; i < n; i += 32) {
-    w.perm[i] = i; iperm[i] = i; wpos[i] = -1; wrow[i] = 0.0; levl[i] = 0;
+    w.perm[i] = i; iperm[i] = i; wpos[i] = -1; wrow[i] = (T)0; levl[i] = 0;
   }
   __syncwarp();
   int npiv = 0, flags = 0;
+  long long n_elim = 0, n_cand = 0;
   double nnz = 0.0;
   for (int r = 0; r < n; ++r) {
     const int part = w.part_of_row[r];
@@ -164,7 +248,7 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
     for (int t = lane; t < len; t += 32) {
       const int f = iperm[ac[t]];
       const double v = av[t];
-      wrow[f] = v;
+      wrow[f] = (T)v;
       wpos[f] = t;
       sh.nz[t] = f;
       ss += v * v;
@@ -180,7 +264,7 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
     nu = warp_sum_int(nu);
     int cnt = len;
     const double norm = sqrt(ss);
-    const double thr = P.drop_tol * norm;
+    const T thr = (T)(P.drop_tol * norm);
     __syncwarp();
     // --- elimination with the previous U rows, in increasing label order ---
     int last = -1;
@@ -218,10 +302,11 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
       }
       if (best == 0x7fffffff) break;
       last = best;
-      const double wk = wrow[best] * udinv[best];
+      ++n_elim;
+      const T wk = wrow[best] * udinv[best];
       __syncwarp();
       if (fabs(wk) < thr) {
-        if (lane == 0) wrow[best] = 0.0;  // dropped multiplier
+        if (lane == 0) wrow[best] = (T)0;  // dropped multiplier
         __syncwarp();
         continue;
       }
@@ -232,11 +317,11 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
         const int t = base + lane;
         const bool valid = t < ul;
         int f = 0;
-        double v = 0.0;
+        T v = 0;
         bool exists = false;
         if (valid) {
-          if (ub >= 0) { f = iperm[ucc[ub + t]]; v = (double)ucv[ub + t]; }
-          else { f = iperm[w.u_col[(size_t)best * capLU + t]]; v = w.u_val64[(size_t)best * capLU + t]; }
+          if (ub >= 0) { f = iperm[ucc[ub + t]]; v = ucv[ub + t]; }
+          else { f = iperm[w.u_col[(size_t)best * capLU + t]]; v = (T)w.u_val64[(size_t)best * capLU + t]; }
           exists = wpos[f] >= 0;
         }
         const unsigned nm = __ballot_sync(0xffffffffu, valid && !exists);
@@ -259,31 +344,34 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
       }
       if (cnt > kMaxRowNZ) { flags |= 2; cnt = kMaxRowNZ; }
     }
+    n_cand += cnt;
     // --- L part: keep the nl + p largest multipliers ---
+    T* selv = reinterpret_cast<T*>(sh.selV);
     int cL = 0;
     for (int base = 0; base < cnt; base += 32) {
       const int t = base + lane;
       bool c = false;
       int f = 0;
-      double v = 0.0;
-      if (t < cnt) { f = sh.nz[t]; v = wrow[f]; c = f < r && v != 0.0; }
+      T v = 0;
+      if (t < cnt) { f = sh.nz[t]; v = wrow[f]; c = f < r && v != (T)0; }
       const unsigned m = __ballot_sync(0xffffffffu, c);
       const int slot = cL + __popc(m & lanemask_lt());
-      if (c && slot < kMaxSel) { sh.selF[slot] = f; sh.selV[slot] = v; }
+      if (c && slot < kMaxSel) { sh.selF[slot] = f; selv[slot] = v; }
       cL += __popc(m);
     }
     if (cL > kMaxSel) { flags |= 2; cL = kMaxSel; }
     __syncwarp();
     const int keepL = nl + pk;
+    select_topk<T>(sh, cL, keepL);
     int nL = 0, levmax = -1;
     for (int base = 0; base < cL; base += 32) {
       const int e = base + lane;
-      const bool k = e < cL && sel_keep(sh, cL, e, keepL);
+      const bool k = e < cL && sh.selK[e];
       const unsigned m = __ballot_sync(0xffffffffu, k);
       const int slot = nL + __popc(m & lanemask_lt());
       if (k && slot < capLU) {
         w.l_col[(size_t)r * capLU + slot] = sh.selF[e];
-        w.l_val64[(size_t)r * capLU + slot] = sh.selV[e];
+        w.l_val64[(size_t)r * capLU + slot] = (double)selv[e];
         levmax = max(levmax, levl[sh.selF[e]]);
       }
       nL += __popc(m);
@@ -292,51 +380,51 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
     if (nL > capLU) { flags |= 2; nL = capLU; }
     __syncwarp();
     // --- U part: entries above threshold, keep the nu + p largest ---
-    double dval = wpos[r] >= 0 ? wrow[r] : 0.0;
+    T dval = wpos[r] >= 0 ? wrow[r] : (T)0;
     int cU = 0;
     for (int base = 0; base < cnt; base += 32) {
       const int t = base + lane;
       bool c = false;
       int f = 0;
-      double v = 0.0;
-      if (t < cnt) { f = sh.nz[t]; v = wrow[f]; c = f > r && fabs(v) >= thr && v != 0.0; }
+      T v = 0;
+      if (t < cnt) { f = sh.nz[t]; v = wrow[f]; c = f > r && fabs(v) >= thr && v != (T)0; }
       const unsigned m = __ballot_sync(0xffffffffu, c);
       const int slot = cU + __popc(m & lanemask_lt());
-      if (c && slot < kMaxSel) { sh.selF[slot] = f; sh.selV[slot] = v; }
+      if (c && slot < kMaxSel) { sh.selF[slot] = f; selv[slot] = v; }
       cU += __popc(m);
     }
     if (cU > kMaxSel) { flags |= 2; cU = kMaxSel; }
     __syncwarp();
     const int keepU = nu + pk;
-    // mark kept entries by negating the label (-f-1); compact afterwards
+    select_topk<T>(sh, cU, keepU);
     bool mykeep[kMaxSel / 32];
 #pragma unroll
     for (int q = 0; q < kMaxSel / 32; ++q) {
       const int e = q * 32 + lane;
-      mykeep[q] = e < cU && sel_keep(sh, cU, e, keepU);
+      mykeep[q] = e < cU && sh.selK[e];
     }
     __syncwarp();
     // pivot: the largest kept U entry (ties: smaller label)
-    double bv = 0.0;
+    T bv = 0;
     int bf = 0x7fffffff;
 #pragma unroll
     for (int q = 0; q < kMaxSel / 32; ++q) {
       const int e = q * 32 + lane;
       if (mykeep[q]) {
-        const double v = fabs(sh.selV[e]);
+        const T v = fabs(selv[e]);
         const int f = sh.selF[e];
         if (v > bv || (v == bv && f < bf)) { bv = v; bf = f; }
       }
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-      const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+      const T v2 = __shfl_xor_sync(0xffffffffu, bv, o);
       const int f2 = __shfl_xor_sync(0xffffffffu, bf, o);
       if (v2 > bv || (v2 == bv && f2 < bf)) { bv = v2; bf = f2; }
     }
     int jm = -1;
-    if (bf != 0x7fffffff && P.permtol * bv > fabs(dval)) jm = bf;
-    double newdiag = dval;
+    if (bf != 0x7fffffff && (T)P.permtol * bv > fabs(dval)) jm = bf;
+    T newdiag = dval;
     if (jm >= 0) {
       // the column labelled jm becomes the diagonal; the old diagonal value moves
       // to label jm (a U-part entry, or nothing if it was zero)
@@ -354,20 +442,20 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
     for (int q = 0; q < kMaxSel / 32; ++q) {
       const int e = q * 32 + lane;
       bool k = mykeep[q];
-      double v = 0.0;
+      T v = 0;
       int f = 0;
       if (k) {
         f = sh.selF[e];
-        v = sh.selV[e];
-        if (f == jm) { v = dval; k = dval != 0.0; }
+        v = selv[e];
+        if (f == jm) { v = dval; k = dval != (T)0; }
       }
       const unsigned m = __ballot_sync(0xffffffffu, k);
       const int slot = nU + __popc(m & lanemask_lt());
       if (k && slot < capLU) {
         const int oc = w.perm[f];  // original column label
         w.u_col[(size_t)r * capLU + slot] = oc;
-        w.u_val64[(size_t)r * capLU + slot] = v;
-        if (uoff && ufill + slot < ucap) { ucc[ufill + slot] = oc; ucv[ufill + slot] = (T)v; }
+        w.u_val64[(size_t)r * capLU + slot] = (double)v;
+        if (uoff && ufill + slot < ucap) { ucc[ufill + slot] = oc; ucv[ufill + slot] = v; }
       }
       nU += __popc(m);
     }
@@ -391,7 +479,7 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
     for (int t = lane; t < cnt; t += 32) {
       const int f = sh.nz[t];
       wpos[f] = -1;
-      wrow[f] = 0.0;
+      wrow[f] = (T)0;
       if (lbits && f < r) { lbits[f >> 5] = 0u; lsum[f >> 10] = 0u; }
     }
     __syncwarp();
@@ -399,9 +487,16 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
   __syncwarp();
   if (sm_work)
     for (int i = lane; i < n; i += 32) w.iperm[i] = iperm[i];
-  if (sm_rows)
-    for (int i = lane; i < n; i += 32) { w.u_dinv64[i] = udinv[i]; w.u_len[i] = ulen_a[i]; w.lev_l[i] = levl[i]; }
+  if (sm_rows) {
+    for (int i = lane; i < n; i += 32) { w.u_dinv64[i] = (double)udinv[i]; w.u_len[i] = ulen_a[i]; w.lev_l[i] = levl[i]; }
+  } else if (sizeof(T) != sizeof(double)) {
+    // udinv aliased the global FP64 array as T values: widen in place, back to front
+    __syncwarp();
+    if (lane == 0)
+      for (int i = n - 1; i >= 0; --i) w.u_dinv64[i] = (double)udinv[i];
+  }
   __syncwarp();
+  if (lane == 0) { w.ctl->ilu_rows += n; w.ctl->ilu_elims += n_elim; w.ctl->ilu_cand += n_cand; }
   *npiv_out = npiv;
   *nnz_out = nnz;
   *p_out = p;
@@ -415,7 +510,7 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
 // Returns the number of chunks.  Block-wide.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ int build_stream(const Walker& w, bool upper, int nlev, Shared& sh) {
+__device__ int build_stream(const Walker& w, const Params& P, bool upper, int nlev, Shared& sh) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   const int* lptr = upper ? w.u_lvl_ptr : w.l_lvl_ptr;
   const int* rows = upper ? w.u_lvl_rows : w.l_lvl_rows;
@@ -425,6 +520,7 @@ __device__ int build_stream(const Walker& w, bool upper, int nlev, Shared& sh) {
   int2* tab = upper ? w.uchunk : w.lchunk;
   unsigned char* stream = upper ? w.ustream : w.lstream;
   const int tsz = (int)sizeof(T), capLU = w.capLU;
+  const int SB = P.slot_bytes;
   // pass A: chunks per level
   for (int lev = wid; lev < nlev; lev += nw) {
     if (lane == 0) {
@@ -435,7 +531,7 @@ __device__ int build_stream(const Walker& w, bool upper, int nlev, Shared& sh) {
         int nr = 0, ne = 0;
         while (q < e && nr < kChunkRows) {
           const int L = len[rows[q]];
-          if (nr > 0 && chunk_bytes(nr + 1, ne + L, tsz, upper) > kSlotBytes) break;
+          if (nr > 0 && chunk_bytes(nr + 1, ne + L, tsz, upper) > SB) break;
           ++nr; ne += L; ++q;
         }
         ++nch;
@@ -456,7 +552,7 @@ __device__ int build_stream(const Walker& w, bool upper, int nlev, Shared& sh) {
         int nr = 0, ne = 0;
         while (q < e && nr < kChunkRows) {
           const int L = len[rows[q]];
-          if (nr > 0 && chunk_bytes(nr + 1, ne + L, tsz, upper) > kSlotBytes) break;
+          if (nr > 0 && chunk_bytes(nr + 1, ne + L, tsz, upper) > SB) break;
           ++nr; ne += L; ++q;
         }
         w.chunk_meta[c] = make_int4(q0, nr, ne, q == e ? 1 : 0);
@@ -481,7 +577,10 @@ __device__ int build_stream(const Walker& w, bool upper, int nlev, Shared& sh) {
     int* cl = st + pad4(nr + 1);
     T* vl = (T*)(cl + pad4(ne));
     T* dv = (T*)((unsigned char*)vl + pad16(tsz * ne));
-    if (lane == 0) *(int4*)base = make_int4(nr, ne, md.w, 0);
+    // lane-group size: up to 4 lanes per row while the rows still fill the CTA once
+    int gs = 0;
+    while (gs < 2 && (nr << (gs + 1)) <= nt) ++gs;
+    if (lane == 0) *(int4*)base = make_int4(nr, ne, md.w, gs);
     if (lane < kMaxSlots) ((int2*)(base + 16))[lane] = c + 1 + lane < nch_total ? tab[c + 1 + lane] : make_int2(0, 0);
     int carry = 0;
     for (int b0 = 0; b0 < nr; b0 += 32) {
@@ -519,7 +618,7 @@ __device__ int build_stream(const Walker& w, bool upper, int nlev, Shared& sh) {
 // Block-wide: relabel U columns to factor labels, compute U levels (warp 0,
 // reverse order) and pack both level sets (counting sort by level).
 template <typename T>
-__device__ __noinline__ void relabel_and_levels(const Walker& w, Shared& sh) {
+__device__ __noinline__ void relabel_and_levels(const Walker& w, const Params& P, Shared& sh) {
   const int n = w.n, tid = threadIdx.x, nt = blockDim.x, capLU = w.capLU;
   for (int idx = tid; idx < n * capLU; idx += nt) {
     const int r = idx / capLU, t = idx - r * capLU;
@@ -565,8 +664,8 @@ __device__ __noinline__ void relabel_and_levels(const Walker& w, Shared& sh) {
   for (int r = tid; r < n; r += nt) w.u_lvl_rows[atomicAdd(&w.lvl_cur[w.lev_u[r]], 1)] = r;
   if (tid == 0) { w.ctl->nlev_l = nll; w.ctl->nlev_u = nlu; }
   __syncthreads();
-  const int ncl = build_stream<T>(w, false, nll, sh);
-  const int ncu = build_stream<T>(w, true, nlu, sh);
+  const int ncl = build_stream<T>(w, P, false, nll, sh);
+  const int ncu = build_stream<T>(w, P, true, nlu, sh);
   if (tid == 0) { w.ctl->nchunk_l = ncl; w.ctl->nchunk_u = ncu; }
   fence_proxy_async_global();  // the streams are read next by bulk (async-proxy) copies
   __syncthreads();
@@ -604,7 +703,7 @@ __device__ __noinline__ int factor_block(const Walker& w, const Params& P, Share
   __syncthreads();
   const int fl = sh.iflag[0];
   const long long tl = clock64();
-  relabel_and_levels<T>(w, sh);
+  relabel_and_levels<T>(w, P, sh);
   if (threadIdx.x == 0) w.ctl->cyc[PH_LEVELS] += clock64() - tl;
   if (threadIdx.x == 0) {
     long long tot = 0;

@@ -54,7 +54,9 @@ class vmc_stats(C.Structure):
                 ("refactors_updates", C.c_int64), ("factorizations", C.c_int64), ("pivots", C.c_int64),
                 ("N_max_seen", C.c_double), ("N_sum", C.c_double), ("nnz_A", C.c_double), ("nnz_LU", C.c_double),
                 ("levels_L", C.c_int), ("levels_U", C.c_int), ("n_updates", C.c_int), ("status", C.c_int),
-                ("its_hist", C.c_int64 * 64), ("phase_cycles", C.c_int64 * 16), ("alg_bytes", C.c_double)]
+                ("its_hist", C.c_int64 * 64), ("phase_cycles", C.c_int64 * 16), ("alg_bytes", C.c_double),
+                ("ilu_rows", C.c_int64), ("ilu_elims", C.c_int64), ("ilu_cand", C.c_int64),
+                ("chunks_L", C.c_int), ("chunks_U", C.c_int)]
 
 
 # name -> (restype, argtypes); every symbol the header declares
@@ -81,6 +83,7 @@ _SIG = {
     "vmc_apply_preconditioner": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "vmc_refactor": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "vmc_philox_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "vmc_kernel_bench": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "vmc_ratio_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
     "vmc_noalloc_capacity": (C.c_size_t, []),
@@ -254,6 +257,10 @@ def vmc_apply_preconditioner(ctx, walker: int, v) -> np.ndarray:
 
 def vmc_refactor(ctx, walker: int, reorder: bool = True) -> None:
     _check(lib().vmc_refactor(ctx, walker, 1 if reorder else 0), ctx)
+
+
+def vmc_kernel_bench(ctx, which: int, reps: int) -> None:
+    _check(lib().vmc_kernel_bench(ctx, which, reps), ctx)
 
 
 def vmc_philox_device(ctr, key) -> np.ndarray:

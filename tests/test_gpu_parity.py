@@ -139,3 +139,23 @@ def test_single_move_api_matches_oracle(vmc):
         assert abs(vmc.vmc_ratio(ctx, 0, 3, R[3]) - 1.0) < 1e-13
     finally:
         vmc.vmc_destroy(ctx)
+
+
+@pytest.mark.parametrize("threads", [64, 128, 512])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_block_sizes_match_oracle(vmc, threads, prec):
+    """The CTA size changes the row-group split and reduction orders, not the ratios;
+    64 threads is one producer warp and a single consumer warp."""
+    wl = WL.PLAIN_216
+    ctx = vmc.vmc_create(wl.systems(), vmc.params(precision=0 if prec == "fp64" else 1, block_threads=threads))
+    try:
+        vmc.vmc_init_positions(ctx, wl.seeds(), wl.jitter)
+        acc, rat = vmc.vmc_sweep(ctx, 2, wl.sigma, wl.seeds())
+        st = vmc.vmc_get_stats(ctx, 0)
+    finally:
+        vmc.vmc_destroy(ctx)
+    s = O.system(6, 0, wl.a, wl.kappa, wl.r_c)
+    R0 = O.initial_positions(s, 1, wl.jitter)
+    _, r_ref, a_ref, u_ref = O.chain(s, 1, wl.sigma, R0, 2, solver=O.SOLVER_SHERMAN_MORRISON)
+    assert compare_chain(rat, acc, r_ref, a_ref, u_ref) > 200
+    assert st["status"] == 0
