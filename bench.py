@@ -188,8 +188,10 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     stream = torch.cuda.current_stream()
+    from paper_1008_5113_gb300 import replicas
+
     systems = [(K_LAT, 0, A, KAPPA, RC)] * WALKERS
-    seeds = [rank * WALKERS + w + 1 for w in range(WALKERS)]
+    seeds = replicas.walker_seeds(rank, WALKERS)
 
     def make(prec, engine, nw=WALKERS):
         ctx = vmc.vmc_create(systems[:nw], vmc.params(precision=prec, engine=engine), stream=stream)
@@ -227,12 +229,8 @@ def main():
     stats = [vmc.vmc_get_stats(ctx, w) for w in range(WALKERS)]
     ratios_local = sum(s["proposals"] for s in stats)
     assert ratios_local == args.steps * WALKERS * N, (ratios_local, args.steps)
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * ratios_local / (t_max / 1000.0)
+    ratios_all, t_max = replicas.reduce_run(ratios_local, total_ms)
+    value = replicas.throughput(ratios_all, t_max / 1000.0)
     alg_bytes = sum(s["alg_bytes"] for s in stats)
     # ---- e2e: public host API, host seeds in, host logs out, every step -------------------
     host_seeds = np.array(seeds, dtype=np.uint64)
@@ -246,11 +244,8 @@ def main():
         assert st == 0, vmc.vmc_last_error(ctx)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * args.steps * WALKERS * N / e2e_s
+    e2e_count, e2e_s = replicas.reduce_run(args.steps * WALKERS * N, e2e_s)
+    e2e_value = replicas.throughput(e2e_count, e2e_s)
     vmc.vmc_destroy(ctx)
 
     extra = {}

@@ -65,7 +65,9 @@ enum {
   VMC_ENGINE_PLAIN = 0,      /* one walker per launch, one launch per move step      */
   VMC_ENGINE_STEP = 1,       /* one launch per move step advancing every walker      */
   VMC_ENGINE_PERSISTENT = 2, /* one launch per sweep, every walker (CTA per walker)  */
-  VMC_ENGINE_DENSE_SM = 3    /* explicit inverse + Sherman-Morrison (Sec. 1), FP64   */
+  VMC_ENGINE_DENSE_SM = 3    /* explicit inverse + Sherman-Morrison (Sec. 1), FP64;
+                                vmc_sweep only (single-move and inspection calls return
+                                VMC_ERR_INVALID); a fresh inverse every sm_refresh sweeps */
 };
 
 /* Solver parameters.  vmc_default_params() fills the defaults noted here. */
@@ -83,7 +85,7 @@ typedef struct {
   int precision;       /* VMC_PREC_FP64 or VMC_PREC_MIXED (MIXED)                         */
   int engine;          /* VMC_ENGINE_* (PERSISTENT)                                        */
   int block_threads;   /* threads per walker CTA: 64..512, multiple of 32; 0 = auto (0)  */
-  int sm_refresh;      /* dense engine: fresh inverse every sm_refresh sweeps (1)          */
+  int sm_refresh;      /* dense engine: fresh inverse every sm_refresh sweeps; 0: never (1) */
 } vmc_solver_params;
 
 /* Per-walker statistics (Sec. 4 Tables 2 and 3 analogues). */
@@ -194,6 +196,11 @@ vmc_status vmc_refactor(vmc_ctx* ctx, int walker, int reorder);
  * alg_bytes statistic grows by the algorithmic bytes moved.  Clobbers the walkers'
  * Krylov work vectors (any pending vmc_ratio is dropped). */
 vmc_status vmc_kernel_bench(vmc_ctx* ctx, int which, int reps);
+/* Failure detection check (tests): launches a kernel that waits on a device barrier
+ * phase nothing completes, with the solver's bounded wait (~1 s); returns
+ * VMC_ERR_TIMEOUT when the wait gave up and reported it, as every bounded wait in the
+ * engine does.  The context stays usable. */
+vmc_status vmc_check_wait_timeout(vmc_ctx* ctx);
 /* Philox4x32-10 on the device for n counters (host arrays ctr: 4n words, key: 2
  * words, out: 4n words): checks the device generator against its definition. */
 vmc_status vmc_philox_device(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n);

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libvmc.so")
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["vmc_engine.cu", "vmc_capi.cu", "vmc_noalloc.cu"]
+SOURCES = ["vmc_engine.cu", "vmc_capi.cu", "vmc_noalloc.cu", "vmc_dense.cu"]
 
 
 def _nvcc() -> str:

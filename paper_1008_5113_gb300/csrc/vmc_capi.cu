@@ -132,6 +132,7 @@ struct vmc_ctx {
   size_t log_cap = 0;
   std::vector<char> pending;
   bool ready = false;
+  bool dense = false;
 };
 
 static vmc_status fail(vmc_ctx* c, vmc_status s, const std::string& msg) {
@@ -182,6 +183,83 @@ struct Carve {
 };
 }  // namespace
 
+// Dense engine (explicit inverse + Sherman-Morrison, Sec. 1): per walker the sparse
+// rows (orbital columns, identity layout), the n x n inverse and two work vectors.
+static vmc_status create_dense(vmc_ctx* ctx, const std::vector<Layout>& lay) {
+  const int nw = ctx->nw;
+  ctx->dense = true;
+  ctx->threads = ctx->prm.block_threads ? ctx->prm.block_threads : 256;
+  ctx->smem = 0;
+  std::vector<std::vector<size_t>> offs(nw);
+  Carve cv;
+  ctx->hw.resize(nw);
+  long long base = 0;
+  for (int w = 0; w < nw; ++w) {
+    const Layout& L = lay[w];
+    const int n = L.n, cap = L.cap;
+    auto& o = offs[w];
+    o.push_back(cv.take<double>((size_t)n * 3));   // Z
+    o.push_back(cv.take<int>(n));                  // identity column map
+    o.push_back(cv.take<double>((size_t)n * 3));   // R
+    o.push_back(cv.take<int>((size_t)n * cap));    // a_col
+    o.push_back(cv.take<double>((size_t)n * cap)); // a_val
+    o.push_back(cv.take<int>(n));                  // a_len
+    o.push_back(cv.take<double>((size_t)n * n));   // B
+    o.push_back(cv.take<double>(n));               // dcol
+    o.push_back(cv.take<double>(n));               // drow
+    o.push_back(cv.take<int>(n));                  // dpiv
+    Walker& W = ctx->hw[w];
+    std::memset(&W, 0, sizeof(W));
+    const vmc_system& s = ctx->sys[w];
+    W.n = n; W.K = s.K; W.lattice = s.lattice; W.cap = cap; W.per = L.per;
+    W.a = s.a; W.kappa = s.kappa; W.rc = s.r_c; W.rc2 = s.r_c * s.r_c; W.L = s.K * s.a;
+    W.log_base = base;
+    base += n;
+    ctx->max_n = std::max(ctx->max_n, n);
+  }
+  ctx->total_n = base;
+  const size_t ctl_off = cv.take<Ctl>(nw);
+  const size_t walk_off = cv.take<Walker>(nw);
+  ctx->arena_bytes = cv.off + 256;
+  cudaError_t e = cudaMalloc((void**)&ctx->arena, ctx->arena_bytes);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc arena");
+  e = cudaMemsetAsync(ctx->arena, 0, ctx->arena_bytes, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemset arena");
+  char* A = ctx->arena;
+  ctx->dCtl = (Ctl*)(A + ctl_off);
+  ctx->dW = (Walker*)(A + walk_off);
+  for (int w = 0; w < nw; ++w) {
+    const auto& o = offs[w];
+    Walker& W = ctx->hw[w];
+    const int n = W.n;
+    W.Z = (const double*)(A + o[0]);
+    W.col_of_orb = (const int*)(A + o[1]);
+    W.orb_of_col = (const int*)(A + o[1]);
+    W.R = (double*)(A + o[2]);
+    W.a_col = (int*)(A + o[3]);
+    W.a_val = (double*)(A + o[4]);
+    W.a_len = (int*)(A + o[5]);
+    W.Bd = (double*)(A + o[6]);
+    W.dcol = (double*)(A + o[7]);
+    W.drow = (double*)(A + o[8]);
+    W.dpiv = (int*)(A + o[9]);
+    W.ctl = ctx->dCtl + w;
+    std::vector<int> ident(n);
+    for (int j = 0; j < n; ++j) ident[j] = j;
+    e = cudaMemcpyAsync((void*)W.Z, lay[w].Z.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((void*)W.col_of_orb, ident.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "upload layout");
+  }
+  e = cudaMemcpyAsync(ctx->dW, ctx->hw.data(), sizeof(Walker) * nw, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_seeds, sizeof(uint64_t) * nw);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload walkers");
+  ctx->pending.assign(nw, 0);
+  return VMC_OK;
+}
+
 extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const vmc_solver_params* params,
                                  void* stream, vmc_ctx** out) {
   if (!out) return VMC_ERR_INVALID;
@@ -198,7 +276,9 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   if (p.gmres_m < 1 || p.gmres_m > kMaxM) st = bad("gmres_m must be in [1, 40]");
   else if (p.max_updates < 0 || p.max_updates > kMaxUpd) st = bad("max_updates must be in [0, 128]");
   else if (p.precision != VMC_PREC_FP64 && p.precision != VMC_PREC_MIXED) st = bad("precision");
-  else if (p.engine < VMC_ENGINE_PLAIN || p.engine > VMC_ENGINE_PERSISTENT) st = bad("engine (dense SM has its own entry)");
+  else if (p.engine < VMC_ENGINE_PLAIN || p.engine > VMC_ENGINE_DENSE_SM) st = bad("engine");
+  else if (p.engine == VMC_ENGINE_DENSE_SM && p.precision != VMC_PREC_FP64) st = bad("the dense engine is FP64 only");
+  else if (p.sm_refresh < 0) st = bad("sm_refresh must be >= 0");
   else if (p.block_threads != 0 && (p.block_threads < 64 || p.block_threads > kMaxThreads || p.block_threads % 32))
     st = bad("block_threads must be 0 or a multiple of 32 in [64, 512]");
   else if (!(p.drop_tol >= 0.0) || !(p.permtol >= 0.0) || p.max_restarts < 0) st = bad("ILUTP/GMRES parameters");
@@ -230,6 +310,11 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
       *out = ctx;
       return VMC_ERR_INVALID;
     }
+  }
+  if (p.engine == VMC_ENGINE_DENSE_SM) {
+    vmc_status ds = create_dense(ctx, lay);
+    *out = ctx;
+    return ds;
   }
   // carve one arena
   const size_t Tsz = ctx->fp64 ? sizeof(double) : sizeof(float);
@@ -440,7 +525,8 @@ static vmc_status check_walker_status(vmc_ctx* ctx) {
 }
 
 static vmc_status setup_all(vmc_ctx* ctx, int w0, int nwalk) {
-  CK(launch_setup(cfg(ctx), ctx->dW, w0, nwalk, ctx->P), "setup kernel");
+  if (ctx->dense) CK(launch_dense_setup(cfg(ctx), ctx->dW + w0, nwalk), "dense setup kernel");
+  else CK(launch_setup(cfg(ctx), ctx->dW, w0, nwalk, ctx->P), "setup kernel");
   for (int w = w0; w < w0 + nwalk; ++w) ctx->pending[w] = 0;
   ctx->ready = true;
   return check_walker_status(ctx);
@@ -478,6 +564,7 @@ extern "C" vmc_status vmc_get_positions(vmc_ctx* ctx, int walker, double* xyz) {
 }
 
 extern "C" vmc_status vmc_ratio(vmc_ctx* ctx, int walker, int k, const double r_new[3], double* ratio) {
+  if (ctx && ctx->dense) return fail(ctx, VMC_ERR_INVALID, "not available with the dense engine");
   if (!ctx || !r_new || !ratio || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
   if (!ctx->ready) return fail(ctx, VMC_ERR_STATE, "positions not set");
   const Walker& W = ctx->hw[walker];
@@ -496,6 +583,7 @@ extern "C" vmc_status vmc_ratio(vmc_ctx* ctx, int walker, int k, const double r_
 }
 
 extern "C" vmc_status vmc_accept(vmc_ctx* ctx, int walker) {
+  if (ctx && ctx->dense) return fail(ctx, VMC_ERR_INVALID, "not available with the dense engine");
   if (!ctx || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
   if (!ctx->pending[walker]) return fail(ctx, VMC_ERR_STATE, "vmc_accept without a pending vmc_ratio");
   CK(launch_accept(cfg(ctx), ctx->dW, walker, ctx->P), "accept kernel");
@@ -521,7 +609,10 @@ static vmc_status enqueue_sweeps(vmc_ctx* ctx, int n_sweeps, double sigma, const
   const LaunchCfg L = cfg(ctx);
   const long long s0 = ctx->sweeps;
   const int eng = ctx->prm.engine;
-  if (eng == VMC_ENGINE_PERSISTENT) {
+  if (eng == VMC_ENGINE_DENSE_SM) {
+    CK(launch_dense_sweep(L, ctx->dW, ctx->nw, n_sweeps, s0, sigma, d_seeds, acc, ratio, ctx->prm.sm_refresh),
+       "dense sweep kernel");
+  } else if (eng == VMC_ENGINE_PERSISTENT) {
     CK(launch_sweep(L, ctx->dW, 0, ctx->nw, ctx->P, n_sweeps, s0, sigma, d_seeds, acc, ratio), "sweep kernel");
   } else if (eng == VMC_ENGINE_STEP) {
     for (int s = 0; s < n_sweeps; ++s)
@@ -639,6 +730,7 @@ static cudaError_t d2h(T* dst, const T* src, size_t count, cudaStream_t s) {
 }
 
 extern "C" vmc_status vmc_get_matrix(vmc_ctx* ctx, int walker, double* A_dense, int* part_of_row, int* orb_of_col) {
+  if (ctx && ctx->dense) return fail(ctx, VMC_ERR_INVALID, "not available with the dense engine");
   if (!ctx || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
   const Walker& W = ctx->hw[walker];
   const int n = W.n, cap = W.cap;
@@ -663,6 +755,7 @@ extern "C" vmc_status vmc_get_matrix(vmc_ctx* ctx, int walker, double* A_dense, 
 }
 
 extern "C" vmc_status vmc_get_factors(vmc_ctx* ctx, int walker, double* L_dense, double* U_dense, int* perm) {
+  if (ctx && ctx->dense) return fail(ctx, VMC_ERR_INVALID, "not available with the dense engine");
   if (!ctx || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
   const Walker& W = ctx->hw[walker];
   const int n = W.n, c = W.capLU;
@@ -696,6 +789,7 @@ extern "C" vmc_status vmc_get_factors(vmc_ctx* ctx, int walker, double* L_dense,
 }
 
 extern "C" vmc_status vmc_apply_preconditioner(vmc_ctx* ctx, int walker, const double* v, double* z) {
+  if (ctx && ctx->dense) return fail(ctx, VMC_ERR_INVALID, "not available with the dense engine");
   if (!ctx || !v || !z || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
   if (!ctx->ready) return fail(ctx, VMC_ERR_STATE, "positions not set");
   const Walker& W = ctx->hw[walker];
@@ -708,6 +802,7 @@ extern "C" vmc_status vmc_apply_preconditioner(vmc_ctx* ctx, int walker, const d
 }
 
 extern "C" vmc_status vmc_refactor(vmc_ctx* ctx, int walker, int reorder) {
+  if (ctx && ctx->dense) return fail(ctx, VMC_ERR_INVALID, "not available with the dense engine");
   if (!ctx || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
   if (!ctx->ready) return fail(ctx, VMC_ERR_STATE, "positions not set");
   CK(launch_refactor(cfg(ctx), ctx->dW, walker, ctx->P, reorder), "refactor kernel");
@@ -716,11 +811,26 @@ extern "C" vmc_status vmc_refactor(vmc_ctx* ctx, int walker, int reorder) {
 }
 
 extern "C" vmc_status vmc_kernel_bench(vmc_ctx* ctx, int which, int reps) {
+  if (ctx && ctx->dense) return fail(ctx, VMC_ERR_INVALID, "not available with the dense engine");
   if (!ctx || which < 0 || which > 2 || reps < 1) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
   if (!ctx->ready) return fail(ctx, VMC_ERR_STATE, "positions not set");
   CK(launch_bench(cfg(ctx), ctx->dW, ctx->nw, ctx->P, which, reps), "bench kernel");
   for (int w = 0; w < ctx->nw; ++w) ctx->pending[w] = 0;
   return VMC_OK;
+}
+
+extern "C" vmc_status vmc_check_wait_timeout(vmc_ctx* ctx) {
+  if (!ctx) return VMC_ERR_INVALID;
+  int* d = nullptr;
+  int h = -1;
+  CK(cudaMalloc((void**)&d, sizeof(int)), "alloc");
+  cudaError_t e = launch_wait_timeout(d, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "wait-timeout kernel");
+  if (h != ST_TIMEOUT) return fail(ctx, VMC_ERR_STATE, "bounded wait did not report a timeout");
+  return fail(ctx, VMC_ERR_TIMEOUT, "device wait gave up after its time limit (expected)");
 }
 
 extern "C" vmc_status vmc_philox_device(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n) {

@@ -100,6 +100,8 @@ struct Walker {
   int* pend_acol; double* pend_aval; int* pend_ucol; double* pend_uval;
   Ctl* ctl;
   long long log_base;     // first log entry of this walker for one sweep (prefix of n)
+  // dense engine (explicit inverse): B row-major n x n, two work vectors, pivots
+  double* Bd; double* dcol; double* drow; int* dpiv;
 };
 
 struct Params {

@@ -372,6 +372,19 @@ __global__ void __launch_bounds__(kMaxThreads) k_bench(const Walker* __restrict_
   }
 }
 
+// Failure-detection check: wait on an mbarrier phase that nothing completes, with
+// the same bounded wait the solver uses; records ST_TIMEOUT when it gives up.
+__global__ void k_wait_timeout(int* status) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0u);  // phase 0 never completes: no arrival is made
+  if (threadIdx.x == 0) *status = ok ? ST_OK : ST_TIMEOUT;
+}
+
 __global__ void k_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -443,6 +456,10 @@ cudaError_t launch_apply_precond(const LaunchCfg& L, const Walker* W, int wi, co
 cudaError_t launch_bench(const LaunchCfg& L, const Walker* W, int nwalk, const Params& P, int which, int reps) {
   if (L.fp64) VMC_LAUNCH(k_bench<double>, nwalk, W, P, which, reps);
   VMC_LAUNCH(k_bench<float>, nwalk, W, P, which, reps);
+}
+cudaError_t launch_wait_timeout(int* status, cudaStream_t s) {
+  k_wait_timeout<<<1, 32, 0, s>>>(status);
+  return cudaGetLastError();
 }
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, cudaStream_t s) {
   k_philox<<<(n + 127) / 128, 128, 0, s>>>(ctr, key, out, n);

@@ -31,6 +31,10 @@ cudaError_t launch_setup(const LaunchCfg& L, const Walker* W, int walker0, int n
 cudaError_t launch_refactor(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int reorder);
 cudaError_t launch_apply_precond(const LaunchCfg& L, const Walker* W, int wi, const Params& P);
 cudaError_t launch_bench(const LaunchCfg& L, const Walker* W, int nwalk, const Params& P, int which, int reps);
+cudaError_t launch_dense_setup(const LaunchCfg& L, const Walker* W, int nwalk);
+cudaError_t launch_dense_sweep(const LaunchCfg& L, const Walker* W, int nwalk, int n_sweeps, long long sweep0,
+                               double sigma, const uint64_t* seeds, uint8_t* acc, double* ratio, int refresh);
+cudaError_t launch_wait_timeout(int* status, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, cudaStream_t s);
 
 // Shared-memory plan of a walker CTA: the solve vector (ybytes) in shared memory when

@@ -84,6 +84,7 @@ _SIG = {
     "vmc_refactor": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "vmc_philox_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "vmc_kernel_bench": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "vmc_check_wait_timeout": (C.c_int, [C.c_void_p]),
     "vmc_ratio_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
     "vmc_noalloc_capacity": (C.c_size_t, []),
@@ -261,6 +262,11 @@ def vmc_refactor(ctx, walker: int, reorder: bool = True) -> None:
 
 def vmc_kernel_bench(ctx, which: int, reps: int) -> None:
     _check(lib().vmc_kernel_bench(ctx, which, reps), ctx)
+
+
+def vmc_check_wait_timeout(ctx) -> int:
+    """Status of the bounded-wait check (VMC_ERR_TIMEOUT = 6 expected)."""
+    return lib().vmc_check_wait_timeout(ctx)
 
 
 def vmc_philox_device(ctr, key) -> np.ndarray:

@@ -159,3 +159,22 @@ def test_block_sizes_match_oracle(vmc, threads, prec):
     _, r_ref, a_ref, u_ref = O.chain(s, 1, wl.sigma, R0, 2, solver=O.SOLVER_SHERMAN_MORRISON)
     assert compare_chain(rat, acc, r_ref, a_ref, u_ref) > 200
     assert st["status"] == 0
+
+
+def test_dense_engine_matches_oracle(vmc):
+    """The explicit-inverse engine (Sec. 1), FP64, with a fresh inverse every sweep."""
+    wl = WL.PLAIN_216
+    ctx = vmc.vmc_create(wl.systems(), vmc.params(precision=0, engine=vmc.ENGINE_DENSE_SM, sm_refresh=1))
+    try:
+        vmc.vmc_init_positions(ctx, wl.seeds(), wl.jitter)
+        acc, rat = vmc.vmc_sweep(ctx, 3, wl.sigma, wl.seeds())
+        st = vmc.vmc_get_stats(ctx, 0)
+        with pytest.raises(vmc.VmcError):
+            vmc.vmc_ratio(ctx, 0, 0, [0.5, 0.5, 0.5])
+    finally:
+        vmc.vmc_destroy(ctx)
+    s = O.system(6, 0, wl.a, wl.kappa, wl.r_c)
+    R0 = O.initial_positions(s, 1, wl.jitter)
+    _, r_ref, a_ref, u_ref = O.chain(s, 1, wl.sigma, R0, 3, solver=O.SOLVER_DENSE_LU)
+    assert compare_chain(rat, acc, r_ref, a_ref, u_ref) > 400
+    assert st["factorizations"] == 3 and st["status"] == 0
