@@ -81,7 +81,7 @@ typedef struct {
   double ratio_tol;    /* goal: predicted relative ratio error (1e-12)                   */
   double N_max;        /* reorder + refactor when the stability monitor N exceeds it (100) */
   double slow_factor;  /* ... or when the iterations reach slow_factor x the average (4)  */
-  int max_updates;     /* refactor after this many rank-one preconditioner updates (32)   */
+  int max_updates;     /* refactor after this many rank-one preconditioner updates (64)   */
   int precision;       /* VMC_PREC_FP64 or VMC_PREC_MIXED (MIXED)                         */
   int engine;          /* VMC_ENGINE_* (PERSISTENT)                                        */
   int block_threads;   /* threads per walker CTA: 64..512, multiple of 32; 0 = auto (0)  */

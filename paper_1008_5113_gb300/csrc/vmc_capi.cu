@@ -162,7 +162,7 @@ extern "C" vmc_status vmc_default_params(vmc_solver_params* p) {
   p->ratio_tol = 1e-12;
   p->N_max = 100.0;
   p->slow_factor = 4.0;
-  p->max_updates = 32;
+  p->max_updates = 64;
   p->precision = VMC_PREC_MIXED;
   p->engine = VMC_ENGINE_PERSISTENT;
   p->block_threads = 0;
@@ -341,7 +341,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     o.push_back(cv.take<int>(n));                      // 9 a_len
     o.push_back(cv.take<int>((size_t)n * capLU));      // 10 l_col
     o.push_back(cv.take<double>((size_t)n * capLU));   // 11 l_val64
-    const size_t sbytes = (size_t)n * (192 + 12 * (size_t)capLU);
+    const size_t sbytes = (size_t)n * (256 + 12 * (size_t)capLU);
     o.push_back(cv.take<unsigned char>(sbytes));       // 12 lstream
     o.push_back(cv.take<int>(n));                      // 13 l_len
     o.push_back(cv.take<int>((size_t)n * capLU));      // 14 u_col
@@ -363,7 +363,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     o.push_back(cv.take<int>(n));                      // 30 wpos
     o.push_back(cv.take<int>(n));                      // 31 gP
     o.push_back(cv.take<int>(n));                      // 32 gQ
-    o.push_back(cv.take<char>((size_t)mu * n * Tsz)); // 33 upd_z
+    o.push_back(cv.take<char>((size_t)((mu + 3) / 4 * 4) * n * Tsz)); // 33 upd_z (transposed)
     o.push_back(cv.take<int>((size_t)mu * kMaxU));     // 34 upd_ucol
     o.push_back(cv.take<char>((size_t)mu * kMaxU * Tsz));  // 35 upd_uval
     o.push_back(cv.take<int>(mu));                     // 36 upd_ulen
@@ -379,10 +379,11 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     o.push_back(cv.take<double>(kMaxU));               // 46 pend_uval
     o.push_back(cv.take<int4>(n + 1));                 // 47 chunk_meta
     o.push_back(cv.take<int>(n + 1));                  // 48 lvl_nchunk
+    o.push_back(cv.take<int4>(2 * (size_t)n + 2));     // 49 seg_meta
     Walker& W = ctx->hw[w];
     std::memset(&W, 0, sizeof(W));
     W.n = n; W.K = systems[w].K; W.lattice = systems[w].lattice; W.cap = cap; W.capLU = capLU;
-    W.m = m; W.mu = mu; W.per = L.per;
+    W.m = m; W.mu = mu; W.mu4 = (mu + 3) / 4 * 4; W.per = L.per;
     W.a = systems[w].a; W.kappa = systems[w].kappa; W.rc = systems[w].r_c;
     W.rc2 = systems[w].r_c * systems[w].r_c; W.L = systems[w].K * systems[w].a;
     W.log_base = base;
@@ -474,6 +475,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     W.pend_uval = (double*)(A + o[46]);
     W.chunk_meta = (int4*)(A + o[47]);
     W.lvl_nchunk = (int*)(A + o[48]);
+    W.seg_meta = (int4*)(A + o[49]);
     W.ctl = ctx->dCtl + w;
     const Layout& L = lay[w];
     e = cudaMemcpyAsync((void*)W.Z, L.Z.data(), sizeof(double) * L.Z.size(), cudaMemcpyHostToDevice, ctx->stream);

@@ -34,6 +34,7 @@ constexpr int kSlotBytes = 8192;  // smallest ring slot (a slot holds the larges
 constexpr int kMaxSlots = 8;      // ring depth (chunks in flight)
 constexpr int kChunkRows = 256;   // rows per chunk at most
 constexpr int kChunkHdr = 80;     // chunk header bytes: int4 + 8 next-chunk descriptors
+constexpr int kMaxSeg = 32;       // levels (segments) per chunk at most
 // phase indices of Ctl::cyc
 enum : int { PH_BUILD = 0, PH_FIRST = 1, PH_REFINE = 2, PH_FACTOR = 3, PH_REORDER = 4, PH_COMMIT = 5, PH_STEP = 6,
              PH_TRI = 7, PH_CHAIN = 8, PH_SPMV = 9, PH_ORTH = 10, PH_RESID = 11, PH_ILUTP = 12, PH_LEVELS = 13, PH_TRIWAIT = 14 };
@@ -73,6 +74,7 @@ struct Ctl {
 // Immutable-per-context description of one walker: sizes and device pointers.
 struct Walker {
   int n, K, lattice, cap, capLU, m, mu;
+  int mu4;                // row stride of the transposed z_hat store (mu rounded up to 4)
   int per;                // sites per cubic cell (1 sc, 2 bcc)
   double a, kappa, rc, rc2, L;
   const double* Z;        // n*3 orbital centres
@@ -88,7 +90,8 @@ struct Walker {
   // level-ordered chunk streams of L and U for the staged triangular solves
   unsigned char* lstream; unsigned char* ustream;
   int2* lchunk; int2* uchunk;   // per chunk {byte offset, bytes}
-  int4* chunk_meta;             // scratch {first row in level order, rows, entries, level end}
+  int4* chunk_meta;             // scratch per chunk {first segment, segments, rows, entries}
+  int4* seg_meta;               // scratch per segment {first row in level order, rows, entries, 0}
   int* lvl_nchunk;              // scratch per level
   int* perm; int* iperm;
   int* lev_l; int* lev_u;
@@ -117,7 +120,8 @@ struct Params {
 
 // Shared memory of a walker CTA (static, < 48 KB).
 struct __align__(16) Shared {
-  unsigned long long bar[kMaxSlots];  // mbarriers of the stream ring
+  unsigned long long bar[kMaxSlots];  // "full" mbarriers of the stream ring
+  unsigned long long ebar[kMaxSlots]; // "empty" mbarriers (released by the consumer warps)
   int ring_seq;                       // chunks consumed so far in this launch
   union {
     struct {                          // GMRES
@@ -194,15 +198,17 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 }
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
-// Byte layout of one stream chunk (all offsets multiples of 16):
-//   int4 header {rows, entries, level_end, log2 of the lane-group size}; int2 next[8]
-//   (descriptors {offset, bytes}
-//   of the following 8 chunks, {0, 0} past the end); int rows[pad4(r)]; int starts[pad4(r+1)];
+// Byte layout of one stream chunk (all offsets multiples of 16): a run of consecutive
+// levels ("segments"; a level too large for one slot is split over several chunks):
+//   int4 header {segments, rows, entries, 0}; int2 next[8] (descriptors {offset, bytes}
+//   of the following 8 chunks, {0, 0} past the end); int4 seg[segments] {first row,
+//   rows, log2 lane-group size, 0}; int rows[pad4(r)]; int starts[pad4(r+1)];
 //   int cols[pad4(e)]; T vals[e] (padded to 16 B); U only: T dinv[r] (padded).
 __host__ __device__ __forceinline__ int pad4(int x) { return (x + 3) & ~3; }
 __host__ __device__ __forceinline__ int pad16(int x) { return (x + 15) & ~15; }
-__host__ __device__ __forceinline__ int chunk_bytes(int r, int e, int tsz, bool upper) {
-  return kChunkHdr + 4 * pad4(r) + 4 * pad4(r + 1) + 4 * pad4(e) + pad16(tsz * e) + (upper ? pad16(tsz * r) : 0);
+__host__ __device__ __forceinline__ int chunk_bytes(int nseg, int r, int e, int tsz, bool upper) {
+  return kChunkHdr + 16 * nseg + 4 * pad4(r) + 4 * pad4(r + 1) + 4 * pad4(e) + pad16(tsz * e) +
+         (upper ? pad16(tsz * r) : 0);
 }
 
 // ---- warp / block reductions (fixed butterfly order: deterministic) ----------

@@ -94,7 +94,7 @@ __device__ __noinline__ void commit_move(const Walker& w, const Params& P, int k
     T* Zh = (T*)w.upd_z;
     T* Uv = (T*)w.upd_uval;
     const double inv = 1.0 / ratio;
-    for (int i = tid; i < n; i += nt) Zh[(size_t)s * n + i] = (T)(w.x64[i] * inv);
+    for (int i = tid; i < n; i += nt) Zh[(size_t)i * w.mu4 + s] = (T)(w.x64[i] * inv);  // transposed
     for (int t = tid; t < ulen; t += nt) {
       w.upd_ucol[(size_t)s * kMaxU + t] = sh.ucol[t];
       Uv[(size_t)s * kMaxU + t] = (T)sh.uval[t];
@@ -106,7 +106,7 @@ __device__ __noinline__ void commit_move(const Walker& w, const Params& P, int k
     for (int t = wid; t < s; t += nw) {
       double acc = 0.0;
       for (int e = lane; e < ulen; e += 32)
-        acc += (double)Uv[(size_t)s * kMaxU + e] * (double)Zh[(size_t)t * n + w.upd_ucol[(size_t)s * kMaxU + e]];
+        acc += (double)Uv[(size_t)s * kMaxU + e] * (double)Zh[(size_t)w.upd_ucol[(size_t)s * kMaxU + e] * w.mu4 + t];
       acc = warp_sum(acc);
       if (lane == 0) w.upd_G[(size_t)s * kMaxUpd + t] = acc;
     }

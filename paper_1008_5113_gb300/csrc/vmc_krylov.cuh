@@ -82,7 +82,10 @@ __device__ __forceinline__ void spmv(const Walker& w, const T* __restrict__ x, T
 // per kernel launch; chunk g of the launch lives in slot g % S, phase (g / S) & 1.
 __device__ __forceinline__ void ring_init(Shared& sh, const Params& P) {
   if (threadIdx.x == 0) {
-    for (int s = 0; s < P.ring_slots; ++s) mbar_init(&sh.bar[s], 1);
+    for (int s = 0; s < P.ring_slots; ++s) {
+      mbar_init(&sh.bar[s], 1);
+      mbar_init(&sh.ebar[s], 1);
+    }
     sh.ring_seq = 0;
     sh.iflag[3] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -90,14 +93,16 @@ __device__ __forceinline__ void ring_init(Shared& sh, const Params& P) {
   __syncthreads();
 }
 
-// One triangular solve in place on y (shared or global), streaming the factor's
-// chunks through the ring with bulk copies issued ring_slots chunks ahead.
+// One triangular solve in place on y (shared or global).  The last warp is the
+// producer: its lane 0 streams the factor's chunks into the ring with bulk copies,
+// refilling a slot once the consumers have released it.  The other warps solve: per
+// chunk they wait for it to land, solve its segments (levels) one after the other
+// with a barrier among the consumer warps between segments, and release the slot.
 // Lower: y_r -= sum_t L_rt y_t.  Upper: y_r = (y_r - sum_t U_rt y_t) / U_rr.
-// Each chunk is one level (or part of one): its rows are independent, solved by
-// lane groups of 2^gs lanes (gs stored in the chunk header); one barrier per chunk.
+// Every wait gives up after ~1 s (status VMC_ERR_TIMEOUT).
 template <typename T>
 __device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, bool upper, T* y, Shared& sh) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nwarp = nt >> 5;
   const unsigned char* stream = upper ? w.ustream : w.lstream;
   const int2* tab = upper ? w.uchunk : w.lchunk;
   const int nch = upper ? w.ctl->nchunk_u : w.ctl->nchunk_l;
@@ -105,59 +110,80 @@ __device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, boo
   const int SB = P.slot_bytes;
   unsigned char* ring = dyn_smem() + P.y_bytes;
   const int seq0 = sh.ring_seq;
+  const int nct = nt - 32;
   long long twait = 0;
-  int slot = seq0 % S;
-  unsigned parity = (unsigned)((seq0 / S) & 1);
-  if (tid == 0) {
-    const int pre = min(S, nch);
-    int sl = slot;
-    for (int c = 0; c < pre; ++c) {
-      const int2 tc = tab[c];
-      mbar_expect_tx(&sh.bar[sl], (unsigned)tc.y);
-      bulk_g2s(ring + (size_t)sl * SB, stream + tc.x, (unsigned)tc.y, &sh.bar[sl]);
-      if (++sl == S) sl = 0;
-    }
-  }
-  for (int c = 0; c < nch; ++c) {
-    const long long tw = clock64();
-    if (!mbar_wait(&sh.bar[slot], parity)) sh.iflag[3] = 1;
-    twait += clock64() - tw;
-    const unsigned char* ch = ring + (size_t)slot * SB;
-    const int4 hd = *(const int4*)ch;
-    const int nr = hd.x, ne = hd.y, gs = hd.w;
-    const int* rws = (const int*)(ch + kChunkHdr);
-    const int* st = rws + pad4(nr);
-    const int* cl = st + pad4(nr + 1);
-    const T* vl = (const T*)(cl + pad4(ne));
-    const T* dv = (const T*)((const unsigned char*)vl + pad16((int)sizeof(T) * ne));
-    const int G = 1 << gs;
-    const int gl = tid & (G - 1);
-    const int ng = (int)(blockDim.x >> gs);
-    for (int base = 0; base < nr; base += ng) {  // same trip count in every lane
-      const int i = base + (tid >> gs);
-      T part = 0;
-      int r = 0;
-      if (i < nr) {
-        r = rws[i];
-        const int e = st[i + 1];
-        for (int t = st[i] + gl; t < e; t += G) part += vl[t] * y[cl[t]];
-      }
-      for (int o = G >> 1; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o, G);
-      if (i < nr && gl == 0) {
-        T acc = y[r] - part;
-        if (upper) acc *= dv[i];
-        y[r] = acc;
+  if (wid == nwarp - 1) {
+    if (lane == 0) {
+      int2 pre[kMaxSlots];
+      for (int k = 0; k < S && k < nch; ++k) pre[k] = tab[k];
+      int slot = seq0 % S;
+      int g = seq0;
+      for (int c = 0; c < nch; ++c, ++g) {
+        unsigned char* dst = ring + (size_t)slot * SB;
+        if (g >= S) {  // the consumers must have released the slot's previous use
+          const long long tw = clock64();
+          if (!mbar_wait(&sh.ebar[slot], (unsigned)(((g / S) - 1) & 1))) sh.iflag[3] = 1;
+          twait += clock64() - tw;
+        }
+        // chunk c's descriptor: from the table for the first S chunks, else from the
+        // header of chunk c - S, still in this slot
+        const int2 tc = c < S ? pre[c] : ((const int2*)(dst + 16))[S - 1];
+        mbar_expect_tx(&sh.bar[slot], (unsigned)tc.y);
+        bulk_g2s(dst, stream + tc.x, (unsigned)tc.y, &sh.bar[slot]);
+        if (++slot == S) slot = 0;
       }
     }
-    // descriptor of chunk c + S, read from this chunk's header before the slot is reused
-    const int2 nx = (tid == 0 && c + S < nch) ? ((const int2*)(ch + 16))[S - 1] : make_int2(0, 0);
-    __syncthreads();
-    if (tid == 0 && c + S < nch) {
-      mbar_expect_tx(&sh.bar[slot], (unsigned)nx.y);
-      bulk_g2s(ring + (size_t)slot * SB, stream + nx.x, (unsigned)nx.y, &sh.bar[slot]);
+  } else {
+    int slot = seq0 % S;
+    unsigned parity = (unsigned)((seq0 / S) & 1);
+    for (int c = 0; c < nch; ++c) {
+      if (!mbar_wait(&sh.bar[slot], parity)) sh.iflag[3] = 1;
+      const unsigned char* ch = ring + (size_t)slot * SB;
+      const int4 hd = *(const int4*)ch;
+      const int nseg = hd.x, nr = hd.y, ne = hd.z;
+      const int4* seg = (const int4*)(ch + kChunkHdr);
+      const int* rws = (const int*)(ch + kChunkHdr + 16 * nseg);
+      const int* st = rws + pad4(nr);
+      const int* cl = st + pad4(nr + 1);
+      const T* vl = (const T*)(cl + pad4(ne));
+      const T* dv = (const T*)((const unsigned char*)vl + pad16((int)sizeof(T) * ne));
+      for (int sgi = 0; sgi < nseg; ++sgi) {
+        const int4 sm = seg[sgi];
+        const int r0 = sm.x, sr = sm.y, gs = sm.z;
+        const int G = 1 << gs;
+        const int gl = tid & (G - 1);
+        const int ng = nct >> gs;
+        for (int base = 0; base < sr; base += ng) {  // same trip count in every lane
+          const int i = r0 + base + (tid >> gs);
+          const bool on = base + (tid >> gs) < sr;
+          T part = 0;
+          int r = 0;
+          if (on) {
+            r = rws[i];
+            const int e = st[i + 1];
+            int t = st[i] + gl;
+            T part2 = 0;
+            for (; t + G < e; t += 2 * G) {  // two entries in flight per lane
+              part += vl[t] * y[cl[t]];
+              part2 += vl[t + G] * y[cl[t + G]];
+            }
+            if (t < e) part += vl[t] * y[cl[t]];
+            part += part2;
+          }
+          for (int o = G >> 1; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o, G);
+          if (on && gl == 0) {
+            T acc = y[r] - part;
+            if (upper) acc *= dv[i];
+            y[r] = acc;
+          }
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(nct) : "memory");  // level barrier (consumers)
+      }
+      if (tid == 0) mbar_arrive(&sh.ebar[slot]);
+      if (++slot == S) { slot = 0; parity ^= 1u; }
     }
-    if (++slot == S) { slot = 0; parity ^= 1u; }
   }
+  __syncthreads();
   if (tid == 0) {
     sh.ring_seq = seq0 + nch;
     w.ctl->cyc[PH_TRIWAIT] += twait;
@@ -187,44 +213,58 @@ __device__ __noinline__ void precond_apply(const Walker& w, const Params& P, con
   __syncthreads();
   const int mu = w.ctl->n_upd;
   if (mu > 0) {
-    const T* Zh = (const T*)w.upd_z;
+    const T* Zt = (const T*)w.upd_z;  // z_hat stored transposed: Zt[i * mu_cap + s]
+    const int mcap = w.mu4;
     const T* Uv = (const T*)w.upd_uval;
-    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-    for (int s = wid; s < mu; s += nw) {       // d_s = u_s^T w_0 (sparse)
-      const int ul = w.upd_ulen[s];
-      const int* uc = w.upd_ucol + (size_t)s * kMaxU;
-      const T* uu = Uv + (size_t)s * kMaxU;
+    const int lane = tid & 31, wid = tid >> 5;
+    // d_s = u_s^T w_0 for all s at once: a lane group per update
+    int gs = 0;
+    while (gs < 5 && (mu << (gs + 1)) <= nt) ++gs;
+    const int G = 1 << gs, gl = tid & (G - 1);
+    for (int base = 0; base < mu; base += (nt >> gs)) {
+      const int s_ = base + (tid >> gs);
       double acc = 0.0;
-      for (int t = lane; t < ul; t += 32) acc += (double)uu[t] * (double)z[uc[t]];
-      acc = warp_sum(acc);
-      if (lane == 0) sh.cupd[s] = acc;
-    }
-    // G[0..mu)[0..mu) staged in the (now idle) stream ring when it fits, then
-    // c_s = d_s - sum_{t<s} G[s][t] c_t by warp 0
-    const bool gs_smem = (size_t)mu * mu * sizeof(double) <= (size_t)P.ring_slots * P.slot_bytes;
-    double* Gs = gs_smem ? (double*)(dyn_smem() + P.y_bytes) : w.upd_G;
-    const int gld = gs_smem ? mu : kMaxUpd;
-    if (gs_smem) {
-      for (int idx = tid; idx < mu * mu; idx += nt) {
-        const int s = idx / mu, t = idx - s * mu;
-        if (t < s) Gs[idx] = w.upd_G[(size_t)s * kMaxUpd + t];
+      if (s_ < mu) {
+        const int ul = w.upd_ulen[s_];
+        const int* uc = w.upd_ucol + (size_t)s_ * kMaxU;
+        const T* uu = Uv + (size_t)s_ * kMaxU;
+        for (int t = gl; t < ul; t += G) acc += (double)uu[t] * (double)z[uc[t]];
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // ring is refilled by bulk copies later
+      for (int o = G >> 1; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+      if (s_ < mu && gl == 0) sh.cupd[s_] = acc;
     }
     __syncthreads();
+    // c_s = d_s - sum_{t<s} G[s][t] c_t: warp 0, lane t holds d_t for t = lane + 32 k;
+    // each solved c_s is broadcast and subtracted from the later d_t
     if (wid == 0) {
-      for (int s = 1; s < mu; ++s) {
-        double acc = 0.0;
-        for (int t = lane; t < s; t += 32) acc += Gs[(size_t)s * gld + t] * sh.cupd[t];
-        acc = warp_sum(acc);
-        if (lane == 0) sh.cupd[s] -= acc;
-        __syncwarp();
+      double d[kMaxUpd / 32];
+#pragma unroll
+      for (int k = 0; k < kMaxUpd / 32; ++k) d[k] = lane + 32 * k < mu ? sh.cupd[lane + 32 * k] : 0.0;
+      for (int s_ = 0; s_ < mu; ++s_) {
+        const double cs = __shfl_sync(0xffffffffu, d[s_ >> 5], s_ & 31);
+#pragma unroll
+        for (int k = 0; k < kMaxUpd / 32; ++k) {
+          const int t = lane + 32 * k;
+          if (t > s_ && t < mu) d[k] -= w.upd_G[(size_t)t * kMaxUpd + s_] * cs;
+        }
       }
+#pragma unroll
+      for (int k = 0; k < kMaxUpd / 32; ++k)
+        if (lane + 32 * k < mu) sh.cupd[lane + 32 * k] = d[k];
     }
     __syncthreads();
-    for (int i = tid; i < n; i += nt) {         // w = w_0 - sum_s z_hat_s c_s
+    // w = w_0 - sum_s z_hat_s c_s: row i of Zt is contiguous over s
+    for (int i = tid; i < n; i += nt) {
+      const T* zr = Zt + (size_t)i * mcap;
       T acc = z[i];
-      for (int s = 0; s < mu; ++s) acc -= Zh[(size_t)s * n + i] * (T)sh.cupd[s];
+      int s_ = 0;
+      for (; s_ + 4 <= mu; s_ += 4) {
+        Vec4<T> v;
+        v.load(zr + s_);
+        acc -= v.v[0] * (T)sh.cupd[s_] + v.v[1] * (T)sh.cupd[s_ + 1] + v.v[2] * (T)sh.cupd[s_ + 2] +
+               v.v[3] * (T)sh.cupd[s_ + 3];
+      }
+      for (; s_ < mu; ++s_) acc -= zr[s_] * (T)sh.cupd[s_];
       z[i] = acc;
     }
     __syncthreads();

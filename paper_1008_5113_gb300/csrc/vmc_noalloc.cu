@@ -107,7 +107,7 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   const int m = p.gmres_m, mu = std::max(1, p.max_updates);
   const int pmax = p.lfil_extra >= 0 ? p.lfil_extra : (cap + 1) / 2;
   const int capLU = cap + pmax + 2;
-  const size_t sbytes = (size_t)n * (192 + 12 * (size_t)capLU);
+  const size_t sbytes = (size_t)n * (256 + 12 * (size_t)capLU);
 
   // carve the walker workspace out of the scratch array
   Off o;
@@ -124,13 +124,14 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   const size_t oLlp = o.take<int>(n + 1), oLlr = o.take<int>(n), oUlp = o.take<int>(n + 1), oUlr = o.take<int>(n);
   const size_t oCur = o.take<int>(n + 1), oWr = o.take<double>(n), oWp = o.take<int>(n);
   const size_t oGP = o.take<int>(n), oGQ = o.take<int>(n);
-  const size_t oUz = o.take<char>((size_t)mu * n * Tsz), oUuc = o.take<int>((size_t)mu * kMaxU);
+  const size_t oUz = o.take<char>((size_t)((mu + 3) / 4 * 4) * n * Tsz), oUuc = o.take<int>((size_t)mu * kMaxU);
   const size_t oUuv = o.take<char>((size_t)mu * kMaxU * Tsz), oUul = o.take<int>(mu);
   const size_t oG = o.take<double>((size_t)kMaxUpd * kMaxUpd);
   const size_t oV = o.take<char>((size_t)(m + 1) * n * Tsz), oZk = o.take<char>((size_t)m * n * Tsz);
   const size_t oTv = o.take<char>((size_t)n * Tsz), oX = o.take<double>(n), oRr = o.take<double>(n);
   const size_t oPac = o.take<int>(cap), oPav = o.take<double>(cap), oPuc = o.take<int>(kMaxU);
   const size_t oPuv = o.take<double>(kMaxU), oMeta = o.take<int4>(n + 1), oLnc = o.take<int>(n + 1);
+  const size_t oSeg = o.take<int4>(2 * (size_t)n + 2);
   const size_t oCtl = o.take<Ctl>(1), oW = o.take<Walker>(1);
   const size_t used = o.off;
   if (used > kNoAllocBytes)
@@ -144,7 +145,7 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
 
   Walker W;
   std::memset(&W, 0, sizeof(W));
-  W.n = n; W.K = sys->K; W.lattice = sys->lattice; W.cap = cap; W.capLU = capLU; W.m = m; W.mu = mu; W.per = lay.per;
+  W.n = n; W.K = sys->K; W.lattice = sys->lattice; W.cap = cap; W.capLU = capLU; W.m = m; W.mu = mu; W.mu4 = (mu + 3) / 4 * 4; W.per = lay.per;
   W.a = sys->a; W.kappa = sys->kappa; W.rc = sys->r_c; W.rc2 = sys->r_c * sys->r_c; W.L = sys->K * sys->a;
   W.Z = (const double*)(base + oZ); W.col_of_orb = (const int*)(base + oCO); W.orb_of_col = (const int*)(base + oOC);
   W.R = (double*)(base + oR); W.row_of_part = (int*)(base + oRP); W.part_of_row = (int*)(base + oPR);
@@ -164,6 +165,7 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   W.pend_acol = (int*)(base + oPac); W.pend_aval = (double*)(base + oPav);
   W.pend_ucol = (int*)(base + oPuc); W.pend_uval = (double*)(base + oPuv);
   W.chunk_meta = (int4*)(base + oMeta); W.lvl_nchunk = (int*)(base + oLnc);
+  W.seg_meta = (int4*)(base + oSeg);
   W.ctl = (Ctl*)(base + oCtl);
   W.log_base = 0;
   Walker* dW = (Walker*)(base + oW);

@@ -505,9 +505,11 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
 
 // ---------------------------------------------------------------------------
 // Level-ordered chunk stream of one triangular factor, consumed by the staged
-// solve: levels in solve order, each level split greedily into chunks of at most
-// kChunkRows rows and kSlotBytes bytes (the rows of a chunk are independent).
-// Returns the number of chunks.  Block-wide.
+// solve.  Consecutive levels are packed into a chunk (one segment each) while it
+// stays within the slot size and kMaxSeg segments; a level larger than a slot is
+// split over chunks.  The rows of a segment are independent.  Returns the number of
+// chunks.  Block-wide (packing by thread 0: sequential over levels, and over rows
+// only inside levels that must be split).
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ int build_stream(const Walker& w, const Params& P, bool upper, int nlev, Shared& sh) {
@@ -521,84 +523,112 @@ __device__ int build_stream(const Walker& w, const Params& P, bool upper, int nl
   unsigned char* stream = upper ? w.ustream : w.lstream;
   const int tsz = (int)sizeof(T), capLU = w.capLU;
   const int SB = P.slot_bytes;
-  // pass A: chunks per level
+  const int nct = nt - 32;  // consumer threads of the solve
+  // entries per level and the level's lane-group size (warp per level).  The group size
+  // is a property of the level, not of the chunk a piece of it lands in, so the rounding
+  // of every row is independent of the slot size.  Enough lanes for <= 2 entries per lane
+  // on the level's longest row (the level barrier waits for it), while the rows still fit
+  // the consumer threads once.  Packed as entries | gs << 28 (entries < 2^28 for K <= 64).
   for (int lev = wid; lev < nlev; lev += nw) {
-    if (lane == 0) {
-      int q = lptr[lev];
-      const int e = lptr[lev + 1];
-      int nch = 0;
-      while (q < e) {
-        int nr = 0, ne = 0;
-        while (q < e && nr < kChunkRows) {
-          const int L = len[rows[q]];
-          if (nr > 0 && chunk_bytes(nr + 1, ne + L, tsz, upper) > SB) break;
-          ++nr; ne += L; ++q;
-        }
-        ++nch;
-      }
-      w.lvl_nchunk[lev] = nch;
+    int e = 0, ml = 0;
+    for (int q = lptr[lev] + lane; q < lptr[lev + 1]; q += 32) {
+      const int L = len[rows[q]];
+      e += L;
+      ml = max(ml, L);
     }
+    e = warp_sum_int(e);
+    ml = warp_max_int(ml);
+    const int lr = lptr[lev + 1] - lptr[lev];
+    int gs = 0;
+    while (gs < 5 && (2 << gs) < ml && (lr << (gs + 1)) <= nct) ++gs;
+    if (lane == 0) w.lvl_nchunk[lev] = e | (gs << 28);
   }
   __syncthreads();
-  const int nch_total = block_scan_inplace(w.lvl_nchunk, nlev, sh);
-  // pass B: chunk metadata and sizes (same greedy rule)
-  for (int lev = wid; lev < nlev; lev += nw) {
-    if (lane == 0) {
+  if (tid == 0) {
+    int nch = 0, nseg = 0;
+    int cs = 0, cr = 0, ce = 0;  // open chunk: segments, rows, entries
+    int c_seg0 = 0;
+    for (int lev = 0; lev < nlev; ++lev) {
       int q = lptr[lev];
-      const int e = lptr[lev + 1];
-      int c = w.lvl_nchunk[lev];
-      while (q < e) {
+      const int qe = lptr[lev + 1];
+      const int lr = qe - q, le = w.lvl_nchunk[lev] & ((1 << 28) - 1), lgs = w.lvl_nchunk[lev] >> 28;
+      if (cs < kMaxSeg && chunk_bytes(cs + 1, cr + lr, ce + le, tsz, upper) <= SB) {
+        w.seg_meta[nseg++] = make_int4(q, lr, le, lgs);  // the whole level joins the open chunk
+        ++cs; cr += lr; ce += le;
+        continue;
+      }
+      while (q < qe) {  // close the open chunk if any, then pieces of this level
+        if (cs > 0 && (cs == kMaxSeg || chunk_bytes(cs + 1, cr + 1, ce + len[rows[q]], tsz, upper) > SB)) {
+          w.chunk_meta[nch] = make_int4(c_seg0, cs, cr, ce);
+          w.lvl_cur[nch] = chunk_bytes(cs, cr, ce, tsz, upper);
+          ++nch; c_seg0 = nseg; cs = 0; cr = 0; ce = 0;
+        }
         const int q0 = q;
-        int nr = 0, ne = 0;
-        while (q < e && nr < kChunkRows) {
+        int pr = 0, pe = 0;
+        while (q < qe) {
           const int L = len[rows[q]];
-          if (nr > 0 && chunk_bytes(nr + 1, ne + L, tsz, upper) > SB) break;
-          ++nr; ne += L; ++q;
+          if ((cr + pr) > 0 && chunk_bytes(cs + 1, cr + pr + 1, ce + pe + L, tsz, upper) > SB) break;
+          ++pr; pe += L; ++q;
         }
-        w.chunk_meta[c] = make_int4(q0, nr, ne, q == e ? 1 : 0);
-        w.lvl_cur[c] = chunk_bytes(nr, ne, tsz, upper);
-        ++c;
+        w.seg_meta[nseg++] = make_int4(q0, pr, pe, lgs);
+        ++cs; cr += pr; ce += pe;
+        if (q < qe) {  // the slot is full: close it
+          w.chunk_meta[nch] = make_int4(c_seg0, cs, cr, ce);
+          w.lvl_cur[nch] = chunk_bytes(cs, cr, ce, tsz, upper);
+          ++nch; c_seg0 = nseg; cs = 0; cr = 0; ce = 0;
+        }
       }
     }
+    if (cs > 0) {
+      w.chunk_meta[nch] = make_int4(c_seg0, cs, cr, ce);
+      w.lvl_cur[nch] = chunk_bytes(cs, cr, ce, tsz, upper);
+      ++nch;
+    }
+    sh.iflag[2] = nch;
   }
   __syncthreads();
+  const int nch_total = sh.iflag[2];
   for (int c = tid; c < nch_total; c += nt) tab[c].y = w.lvl_cur[c];
   __syncthreads();
   block_scan_inplace(w.lvl_cur, nch_total, sh);
   for (int c = tid; c < nch_total; c += nt) tab[c].x = w.lvl_cur[c];
   __syncthreads();
-  // pass C: fill the chunks, one warp per chunk
+  // fill the chunks, one warp per chunk
   for (int c = wid; c < nch_total; c += nw) {
-    const int4 md = w.chunk_meta[c];
-    const int q0 = md.x, nr = md.y, ne = md.z;
+    const int4 cm = w.chunk_meta[c];
+    const int seg0 = cm.x, nseg = cm.y, nr = cm.z, ne = cm.w;
     unsigned char* base = stream + tab[c].x;
-    int* rws = (int*)(base + kChunkHdr);
+    int4* seg = (int4*)(base + kChunkHdr);
+    int* rws = (int*)(base + kChunkHdr + 16 * nseg);
     int* st = rws + pad4(nr);
     int* cl = st + pad4(nr + 1);
     T* vl = (T*)(cl + pad4(ne));
     T* dv = (T*)((unsigned char*)vl + pad16(tsz * ne));
-    // lane-group size: up to 4 lanes per row while the rows still fill the CTA once
-    int gs = 0;
-    while (gs < 2 && (nr << (gs + 1)) <= nt) ++gs;
-    if (lane == 0) *(int4*)base = make_int4(nr, ne, md.w, gs);
+    if (lane == 0) *(int4*)base = make_int4(nseg, nr, ne, 0);
     if (lane < kMaxSlots) ((int2*)(base + 16))[lane] = c + 1 + lane < nch_total ? tab[c + 1 + lane] : make_int2(0, 0);
-    int carry = 0;
-    for (int b0 = 0; b0 < nr; b0 += 32) {
-      const int i = b0 + lane;
-      const int r = i < nr ? rows[q0 + i] : 0;
-      const int L = i < nr ? len[r] : 0;
-      int inc = L;
+    int rbase = 0, carry = 0;
+    for (int sgi = 0; sgi < nseg; ++sgi) {
+      const int4 sm = w.seg_meta[seg0 + sgi];
+      const int q0 = sm.x, sr = sm.y;
+      if (lane == 0) seg[sgi] = make_int4(rbase, sr, sm.w, 0);
+      for (int b0 = 0; b0 < sr; b0 += 32) {
+        const int i = b0 + lane;
+        const int r = i < sr ? rows[q0 + i] : 0;
+        const int L = i < sr ? len[r] : 0;
+        int inc = L;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += v;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += v;
+        }
+        if (i < sr) {
+          rws[rbase + i] = r;
+          st[rbase + i] = carry + inc - L;
+          if (upper) dv[rbase + i] = (T)w.u_dinv64[r];
+        }
+        carry += __shfl_sync(0xffffffffu, inc, 31);
       }
-      if (i < nr) {
-        rws[i] = r;
-        st[i] = carry + inc - L;
-        if (upper) dv[i] = (T)w.u_dinv64[r];
-      }
-      carry += __shfl_sync(0xffffffffu, inc, 31);
+      rbase += sr;
     }
     if (lane == 0) st[nr] = carry;
     __syncwarp();
