@@ -60,7 +60,14 @@ typedef struct {
   double r_c;     /* orbital cutoff radius                     */
 } vmc_system;
 
-enum { VMC_PREC_FP64 = 0, VMC_PREC_MIXED = 1 };
+/* Precision (the precision split of Sec. 3.2 on GB300):
+ *   FP64        : everything in FP64.
+ *   MIXED       : ILUTP factorisation (pivot selection, elimination, dropping) in FP64,
+ *                 factors stored and applied in FP32, inner GMRES in FP32; FP64 outer
+ *                 refinement residual e_i - A x, ratio 1 + u^T x and stability monitor.
+ *   MIXED_F32ILU: as MIXED but the ILUTP working row is FP32 too (faster refactoring;
+ *                 the stored factors are FP32 in both mixed modes). */
+enum { VMC_PREC_FP64 = 0, VMC_PREC_MIXED = 1, VMC_PREC_MIXED_F32ILU = 2 };
 enum {
   VMC_ENGINE_PLAIN = 0,      /* one walker per launch, one launch per move step      */
   VMC_ENGINE_STEP = 1,       /* one launch per move step advancing every walker      */
@@ -82,10 +89,19 @@ typedef struct {
   double N_max;        /* reorder + refactor when the stability monitor N exceeds it (100) */
   double slow_factor;  /* ... or when the iterations reach slow_factor x the average (4)  */
   int max_updates;     /* refactor after this many rank-one preconditioner updates (64)   */
-  int precision;       /* VMC_PREC_FP64 or VMC_PREC_MIXED (MIXED)                         */
+  int precision;       /* VMC_PREC_* (MIXED)                                               */
   int engine;          /* VMC_ENGINE_* (PERSISTENT)                                        */
   int block_threads;   /* threads per walker CTA: 64..512, multiple of 32; 0 = auto (0)  */
   int sm_refresh;      /* dense engine: fresh inverse every sm_refresh sweeps; 0: never (1) */
+  int refactor_lag;    /* PERSISTENT engine: background refactorisation.  A second CTA per
+                          walker (a cluster of two) factors a snapshot of A taken once the
+                          update chain holds refactor_lag updates past its root; the solver
+                          adopts those factors exactly refactor_lag accepts later (waiting for
+                          them if need be) and keeps only the newer chain entries (Sec. 3.2
+                          Eqs. 16-18 hold for any root), so results do not depend on timing.
+                          0: off (refactor in line when the chain is full); > 0: on, clamped
+                          to max_updates / 2; -1: auto -- on with max_updates / 2 when every
+                          walker pair fits on the GPU at once (2 x walkers <= SMs) (-1) */
 } vmc_solver_params;
 
 /* Per-walker statistics (Sec. 4 Tables 2 and 3 analogues). */
@@ -111,13 +127,19 @@ typedef struct {
                                 3 factorisation incl. reorder, 4 reordering, 5 commit + update,
                                 6 whole steps, 7 triangular solves, 8 update-chain apply,
                                 9 SpMV, 10 orthogonalisation + Givens, 11 FP64 residuals,
-                                12 ILUTP rows, 13 level sets + streams, 14 waits for
-                                triangular-factor chunks (inside 7), 15 unused */
+                                12 ILUTP rows, 13 level sets + streams, 14 producer waits
+                                for a free ring slot (inside 7), 15 consumer waits for
+                                triangular-factor chunks to land (inside 7) */
   double alg_bytes;          /* algorithmic (compulsory) bytes of the solves: per phase the
                                 matrix/factor values and indices, the vectors read and written */
   int64_t ilu_rows, ilu_elims, ilu_cand; /* ILUTP rows factored, eliminations performed, and
                                 working-row entries before dropping (summed over rows) */
   int chunks_L, chunks_U;    /* stream chunks of the triangular solves (>= levels)         */
+  int64_t refactors_async;   /* factorisations adopted from the background factor CTA      */
+  int64_t async_wait_cycles; /* solver cycles spent waiting for / adopting them            */
+  int64_t async_factor_cycles; /* factor-CTA cycles spent factoring (off the solver's path) */
+  int factor_set;            /* factor set in use (0 or 1)                                  */
+  int async_lag;             /* the refactor_lag in effect (0: in-line refactorisation)     */
 } vmc_stats;
 
 /* Fill p with the defaults above. */

@@ -133,6 +133,13 @@ struct vmc_ctx {
   std::vector<char> pending;
   bool ready = false;
   bool dense = false;
+  // background refactorisation: second factor set views, factor-CTA views, launch ids
+  bool pair = false;
+  std::vector<Walker> hw1, hwf;
+  Walker* dW1 = nullptr;
+  Walker* dWf = nullptr;
+  Ctl* dShadow = nullptr;
+  int launch_seq = 0;
 };
 
 static vmc_status fail(vmc_ctx* c, vmc_status s, const std::string& msg) {
@@ -167,6 +174,7 @@ extern "C" vmc_status vmc_default_params(vmc_solver_params* p) {
   p->engine = VMC_ENGINE_PERSISTENT;
   p->block_threads = 0;
   p->sm_refresh = 1;
+  p->refactor_lag = -1;
   return VMC_OK;
 }
 
@@ -275,13 +283,15 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   vmc_status st = VMC_OK;
   if (p.gmres_m < 1 || p.gmres_m > kMaxM) st = bad("gmres_m must be in [1, 40]");
   else if (p.max_updates < 0 || p.max_updates > kMaxUpd) st = bad("max_updates must be in [0, 128]");
-  else if (p.precision != VMC_PREC_FP64 && p.precision != VMC_PREC_MIXED) st = bad("precision");
+  else if (p.precision != VMC_PREC_FP64 && p.precision != VMC_PREC_MIXED && p.precision != VMC_PREC_MIXED_F32ILU)
+    st = bad("precision");
   else if (p.engine < VMC_ENGINE_PLAIN || p.engine > VMC_ENGINE_DENSE_SM) st = bad("engine");
   else if (p.engine == VMC_ENGINE_DENSE_SM && p.precision != VMC_PREC_FP64) st = bad("the dense engine is FP64 only");
   else if (p.sm_refresh < 0) st = bad("sm_refresh must be >= 0");
   else if (p.block_threads != 0 && (p.block_threads < 64 || p.block_threads > kMaxThreads || p.block_threads % 32))
     st = bad("block_threads must be 0 or a multiple of 32 in [64, 512]");
   else if (!(p.drop_tol >= 0.0) || !(p.permtol >= 0.0) || p.max_restarts < 0) st = bad("ILUTP/GMRES parameters");
+  else if (p.refactor_lag < -1) st = bad("refactor_lag must be >= -1");
   if (st != VMC_OK) { *out = ctx; return st; }
   ctx->fp64 = p.precision == VMC_PREC_FP64;
   ctx->threads = p.block_threads ? p.block_threads : 256;
@@ -293,8 +303,21 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   ctx->P.max_updates = p.max_updates;
   ctx->P.inner_rtol = p.inner_rtol > 0.0 ? p.inner_rtol : (ctx->fp64 ? 1e-10 : 1e-5);
   ctx->P.ratio_tol = p.ratio_tol > 0.0 ? p.ratio_tol : 1e-12;
+  ctx->P.ilu64 = p.precision != VMC_PREC_MIXED_F32ILU;
   ctx->P.N_max = p.N_max;
   ctx->P.slow_factor = p.slow_factor;
+  {
+    // background refactorisation (persistent engine): needs a chain of >= 2 updates
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int lag = p.refactor_lag;
+    if (lag < 0) lag = (nsm > 0 && 2 * n_walkers <= nsm) ? p.max_updates / 2 : 0;
+    lag = std::min(lag, p.max_updates / 2);
+    if (p.engine != VMC_ENGINE_PERSISTENT) lag = 0;
+    ctx->P.af_lag = std::max(lag, 0);
+    ctx->pair = ctx->P.af_lag > 0;
+  }
 
   // layouts (one per distinct system)
   std::vector<Layout> lay(n_walkers);
@@ -380,6 +403,37 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     o.push_back(cv.take<int4>(n + 1));                 // 47 chunk_meta
     o.push_back(cv.take<int>(n + 1));                  // 48 lvl_nchunk
     o.push_back(cv.take<int4>(2 * (size_t)n + 2));     // 49 seg_meta
+    if (ctx->pair) {
+      // second factor set (same order as offsets 10-30, 47-49), then the snapshot of A
+      o.push_back(cv.take<int>((size_t)n * capLU));    // 50 l_col
+      o.push_back(cv.take<double>((size_t)n * capLU)); // 51 l_val64
+      o.push_back(cv.take<unsigned char>(sbytes));     // 52 lstream
+      o.push_back(cv.take<int>(n));                    // 53 l_len
+      o.push_back(cv.take<int>((size_t)n * capLU));    // 54 u_col
+      o.push_back(cv.take<double>((size_t)n * capLU)); // 55 u_val64
+      o.push_back(cv.take<unsigned char>(sbytes));     // 56 ustream
+      o.push_back(cv.take<int>(n));                    // 57 u_len
+      o.push_back(cv.take<double>(n));                 // 58 u_dinv64
+      o.push_back(cv.take<int2>(2 * (size_t)n + 2));   // 59 lchunk | uchunk
+      o.push_back(cv.take<int>(n));                    // 60 perm
+      o.push_back(cv.take<int>(n));                    // 61 iperm
+      o.push_back(cv.take<int>(n));                    // 62 lev_l
+      o.push_back(cv.take<int>(n));                    // 63 lev_u
+      o.push_back(cv.take<int>(n + 1));                // 64 l_lvl_ptr
+      o.push_back(cv.take<int>(n));                    // 65 l_lvl_rows
+      o.push_back(cv.take<int>(n + 1));                // 66 u_lvl_ptr
+      o.push_back(cv.take<int>(n));                    // 67 u_lvl_rows
+      o.push_back(cv.take<int>(n + 1));                // 68 lvl_cur
+      o.push_back(cv.take<double>(n));                 // 69 wrow
+      o.push_back(cv.take<int>(n));                    // 70 wpos
+      o.push_back(cv.take<int4>(n + 1));               // 71 chunk_meta
+      o.push_back(cv.take<int>(n + 1));                // 72 lvl_nchunk
+      o.push_back(cv.take<int4>(2 * (size_t)n + 2));   // 73 seg_meta
+      o.push_back(cv.take<int>(n));                    // 74 snap_len
+      o.push_back(cv.take<int>((size_t)n * cap));      // 75 snap_col
+      o.push_back(cv.take<double>((size_t)n * cap));   // 76 snap_val
+      o.push_back(cv.take<int>(n));                    // 77 snap_part
+    }
     Walker& W = ctx->hw[w];
     std::memset(&W, 0, sizeof(W));
     W.n = n; W.K = systems[w].K; W.lattice = systems[w].lattice; W.cap = cap; W.capLU = capLU;
@@ -414,6 +468,9 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   }
   const size_t ctl_off = cv.take<Ctl>(n_walkers);
   const size_t walk_off = cv.take<Walker>(n_walkers);
+  const size_t shadow_off = ctx->pair ? cv.take<Ctl>(n_walkers) : 0;
+  const size_t walk1_off = ctx->pair ? cv.take<Walker>(n_walkers) : 0;
+  const size_t walkf_off = ctx->pair ? cv.take<Walker>(2 * (size_t)n_walkers) : 0;
   ctx->arena_bytes = cv.off + 256;
   cudaError_t e = cudaMalloc((void**)&ctx->arena, ctx->arena_bytes);
   if (e != cudaSuccess) { *out = ctx; return cuda_fail(ctx, e, "cudaMalloc arena"); }
@@ -484,6 +541,76 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     if (e == cudaSuccess)
       e = cudaMemcpyAsync((void*)W.orb_of_col, L.orb_of_col.data(), sizeof(int) * L.n, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) { *out = ctx; return cuda_fail(ctx, e, "upload layout"); }
+  }
+  if (ctx->pair) {
+    // views: hw1 = the walker with factor set 1; hwf[2w + s] = the factor CTA's view
+    // (factor set s, matrix = the snapshot, controller = the shadow)
+    ctx->dShadow = (Ctl*)(A + shadow_off);
+    ctx->dW1 = (Walker*)(A + walk1_off);
+    ctx->dWf = (Walker*)(A + walkf_off);
+    ctx->hw1 = ctx->hw;
+    ctx->hwf.assign(2 * (size_t)n_walkers, Walker{});
+    for (int w = 0; w < n_walkers; ++w) {
+      const auto& o = offs[w];
+      Walker& W0 = ctx->hw[w];
+      Walker& W1 = ctx->hw1[w];
+      W1.l_col = (int*)(A + o[50]);
+      W1.l_val64 = (double*)(A + o[51]);
+      W1.lstream = (unsigned char*)(A + o[52]);
+      W1.l_len = (int*)(A + o[53]);
+      W1.u_col = (int*)(A + o[54]);
+      W1.u_val64 = (double*)(A + o[55]);
+      W1.ustream = (unsigned char*)(A + o[56]);
+      W1.u_len = (int*)(A + o[57]);
+      W1.u_dinv64 = (double*)(A + o[58]);
+      W1.lchunk = (int2*)(A + o[59]);
+      W1.uchunk = W1.lchunk + (W1.n + 1);
+      W1.perm = (int*)(A + o[60]);
+      W1.iperm = (int*)(A + o[61]);
+      W1.lev_l = (int*)(A + o[62]);
+      W1.lev_u = (int*)(A + o[63]);
+      W1.l_lvl_ptr = (int*)(A + o[64]);
+      W1.l_lvl_rows = (int*)(A + o[65]);
+      W1.u_lvl_ptr = (int*)(A + o[66]);
+      W1.u_lvl_rows = (int*)(A + o[67]);
+      W1.lvl_cur = (int*)(A + o[68]);
+      W1.wrow = (double*)(A + o[69]);
+      W1.wpos = (int*)(A + o[70]);
+      W1.chunk_meta = (int4*)(A + o[71]);
+      W1.lvl_nchunk = (int*)(A + o[72]);
+      W1.seg_meta = (int4*)(A + o[73]);
+      W0.snap_len = (int*)(A + o[74]);
+      W0.snap_col = (int*)(A + o[75]);
+      W0.snap_val = (double*)(A + o[76]);
+      W0.snap_part = (int*)(A + o[77]);
+      W0.shadow = ctx->dShadow + w;
+      W0.set_id = 0;
+      W1.set_id = 1;
+      for (int sset = 0; sset < 2; ++sset) {
+        Walker F = sset ? W1 : W0;
+        F.a_col = W0.snap_col;
+        F.a_val = W0.snap_val;
+        F.a_len = W0.snap_len;
+        F.part_of_row = W0.snap_part;
+        F.ctl = W0.shadow;
+        F.alt = nullptr;
+        F.fact[0] = F.fact[1] = nullptr;
+        ctx->hwf[2 * (size_t)w + sset] = F;
+      }
+      W0.alt = ctx->dW1 + w;
+      W0.fact[0] = ctx->dWf + 2 * (size_t)w;
+      W0.fact[1] = ctx->dWf + 2 * (size_t)w + 1;
+      W1.alt = nullptr;
+      W1.fact[0] = W0.fact[0];
+      W1.fact[1] = W0.fact[1];
+      W1.snap_len = W0.snap_len; W1.snap_col = W0.snap_col; W1.snap_val = W0.snap_val; W1.snap_part = W0.snap_part;
+      W1.shadow = W0.shadow;
+    }
+    e = cudaMemcpyAsync(ctx->dW1, ctx->hw1.data(), sizeof(Walker) * n_walkers, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->dWf, ctx->hwf.data(), sizeof(Walker) * 2 * n_walkers, cudaMemcpyHostToDevice,
+                          ctx->stream);
+    if (e != cudaSuccess) { *out = ctx; return cuda_fail(ctx, e, "upload walker views"); }
   }
   e = cudaMemcpyAsync(ctx->dW, ctx->hw.data(), sizeof(Walker) * n_walkers, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_seeds, sizeof(uint64_t) * n_walkers);
@@ -614,6 +741,10 @@ static vmc_status enqueue_sweeps(vmc_ctx* ctx, int n_sweeps, double sigma, const
   if (eng == VMC_ENGINE_DENSE_SM) {
     CK(launch_dense_sweep(L, ctx->dW, ctx->nw, n_sweeps, s0, sigma, d_seeds, acc, ratio, ctx->prm.sm_refresh),
        "dense sweep kernel");
+  } else if (eng == VMC_ENGINE_PERSISTENT && ctx->pair) {
+    if (++ctx->launch_seq <= 0) ctx->launch_seq = 1;
+    CK(launch_sweep_pair(L, ctx->dW, 0, ctx->nw, ctx->P, n_sweeps, s0, sigma, d_seeds, acc, ratio, ctx->launch_seq),
+       "sweep kernel (walker pairs)");
   } else if (eng == VMC_ENGINE_PERSISTENT) {
     CK(launch_sweep(L, ctx->dW, 0, ctx->nw, ctx->P, n_sweeps, s0, sigma, d_seeds, acc, ratio), "sweep kernel");
   } else if (eng == VMC_ENGINE_STEP) {
@@ -702,6 +833,11 @@ extern "C" vmc_status vmc_get_stats(vmc_ctx* ctx, int walker, vmc_stats* out) {
   out->ilu_cand = h.ilu_cand;
   out->chunks_L = h.nchunk_l;
   out->chunks_U = h.nchunk_u;
+  out->refactors_async = h.refactors_async;
+  out->async_wait_cycles = h.af_wait_cyc;
+  out->async_factor_cycles = h.af_factor_cyc;
+  out->factor_set = h.active;
+  out->async_lag = ctx->P.af_lag;
   return VMC_OK;
 }
 
@@ -719,6 +855,7 @@ extern "C" vmc_status vmc_reset_stats(vmc_ctx* ctx) {
     for (long long& b : c.cyc) b = 0;
     c.alg_bytes = 0.0;
     c.ilu_rows = c.ilu_elims = c.ilu_cand = 0;
+    c.refactors_async = c.af_wait_cyc = c.af_factor_cyc = 0;
   }
   CK(cudaMemcpyAsync(ctx->dCtl, h.data(), sizeof(Ctl) * ctx->nw, cudaMemcpyHostToDevice, ctx->stream), "stats");
   CK(cudaStreamSynchronize(ctx->stream), "synchronize");
@@ -759,7 +896,12 @@ extern "C" vmc_status vmc_get_matrix(vmc_ctx* ctx, int walker, double* A_dense, 
 extern "C" vmc_status vmc_get_factors(vmc_ctx* ctx, int walker, double* L_dense, double* U_dense, int* perm) {
   if (ctx && ctx->dense) return fail(ctx, VMC_ERR_INVALID, "not available with the dense engine");
   if (!ctx || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
-  const Walker& W = ctx->hw[walker];
+  int set = 0;
+  if (ctx->pair) {
+    CK(cudaMemcpyAsync(&set, &ctx->dCtl[walker].active, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "factor set");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  }
+  const Walker& W = set ? ctx->hw1[walker] : ctx->hw[walker];
   const int n = W.n, c = W.capLU;
   std::vector<int> lc((size_t)n * c), ll(n), uc((size_t)n * c), ul(n), pm(n);
   std::vector<double> lv((size_t)n * c), uv((size_t)n * c), dv(n);

@@ -37,7 +37,8 @@ constexpr int kChunkHdr = 80;     // chunk header bytes: int4 + 8 next-chunk des
 constexpr int kMaxSeg = 32;       // levels (segments) per chunk at most
 // phase indices of Ctl::cyc
 enum : int { PH_BUILD = 0, PH_FIRST = 1, PH_REFINE = 2, PH_FACTOR = 3, PH_REORDER = 4, PH_COMMIT = 5, PH_STEP = 6,
-             PH_TRI = 7, PH_CHAIN = 8, PH_SPMV = 9, PH_ORTH = 10, PH_RESID = 11, PH_ILUTP = 12, PH_LEVELS = 13, PH_TRIWAIT = 14 };
+             PH_TRI = 7, PH_CHAIN = 8, PH_SPMV = 9, PH_ORTH = 10, PH_RESID = 11, PH_ILUTP = 12, PH_LEVELS = 13, PH_TRIWAIT = 14,
+             PH_TRIDATA = 15 };
 
 // status codes (mirror vmc_status)
 enum : int {
@@ -69,6 +70,18 @@ struct Ctl {
   double alg_bytes;   // compulsory (algorithmic) bytes moved by the solves, counted per phase
   long long ilu_rows, ilu_elims, ilu_cand;  // ILUTP rows, eliminations, working-row entries
   int upd_nnz;        // total nonzeros of the u vectors in the update chain
+  // Background refactorisation (persistent engine with a factor CTA per walker).  The
+  // solver uses factor set `active`; the factor CTA fills set af_target from a snapshot
+  // of A taken when the chain held af_snap updates.
+  int active;         // factor set in use (0 or 1)
+  int af_state;       // 0 idle, 1 requested, 2 result ready (written with release order)
+  int af_target;      // factor set being filled
+  int af_snap;        // chain length at the snapshot
+  int af_epoch;       // bumped by every factorisation on this controller
+  int af_epoch_req;   // af_epoch when the request in flight was made
+  int af_stop;        // launch id after which the factor CTA leaves
+  int af_fail;        // the last background factorisation reported (bit 0 breakdown, bit 1 capacity)
+  long long refactors_async, af_wait_cyc, af_factor_cyc;
 };
 
 // Immutable-per-context description of one walker: sizes and device pointers.
@@ -105,7 +118,20 @@ struct Walker {
   long long log_base;     // first log entry of this walker for one sweep (prefix of n)
   // dense engine (explicit inverse): B row-major n x n, two work vectors, pivots
   double* Bd; double* dcol; double* drow; int* dpiv;
+  // background refactorisation: the same walker with the other factor set (nullptr when
+  // the context has one set), and the factor CTA's views (factor set s, the snapshot of
+  // A as its matrix, the shadow controller as its ctl)
+  const Walker* alt;
+  const Walker* fact[2];
+  int set_id;
+  int* snap_len; int* snap_col; double* snap_val; int* snap_part;
+  Ctl* shadow;
 };
+
+// The view of walker w0 (factor set 0) that the solver uses now.
+__device__ __forceinline__ const Walker& active_of(const Walker& w0) {
+  return (w0.alt != nullptr && w0.ctl->active) ? *w0.alt : w0;
+}
 
 struct Params {
   double drop_tol, permtol;
@@ -116,6 +142,8 @@ struct Params {
   int y_bytes;      // bytes reserved for it (multiple of 128)
   int slot_bytes;   // bytes of one ring slot = largest stream chunk (multiple of 16)
   int dsm_bytes;    // total dynamic shared memory (ILUTP scratch may use all of it)
+  int ilu64;        // 1: the ILUTP working row is FP64 whatever the stored precision
+  int af_lag;       // background refactorisation: accepts between a snapshot and its use (0: off)
 };
 
 // Shared memory of a walker CTA (static, < 48 KB).
@@ -197,6 +225,30 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   }
 }
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// Longest wait between the two CTAs of a walker pair (either side), in ns.
+constexpr unsigned long long kPairWaitNs = 30ull * 1000000000ull;
+// Wait (thread 0) until *state differs from `from`; returns the new value, or -1 after
+// kPairWaitNs.
+__device__ __forceinline__ int wait_state_change(const int* state, int from) {
+  int v = ld_acquire(state);
+  if (v != from) return v;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    __nanosleep(1000);
+    v = ld_acquire(state);
+    if (v != from) return v;
+    if (global_ns() - t0 > kPairWaitNs) return -1;
+  }
+}
 
 // Byte layout of one stream chunk (all offsets multiples of 16): a run of consecutive
 // levels ("segments"; a level too large for one slot is split over several chunks):

@@ -183,6 +183,191 @@ __device__ __noinline__ void mc_step(const Walker& w, const Params& P, int k, ui
 }
 
 // ---------------------------------------------------------------------------
+// Background refactorisation (k_sweep_pair).  The second CTA of a walker's cluster
+// factors a snapshot of A while the first keeps stepping, and the solver then re-roots
+// the update chain on the new factors.  With U_s = I - z_hat_s u_s^T the identity
+// A_{s+1} M_{s+1} = A_s M_s (Sec. 3.2 Eqs. 16-18) holds whatever M the chain starts
+// from, so after the swap the solver applies U_{m-1} ... U_{s0} (LU of A_{s0})^{-1} and
+// drops the updates older than the snapshot s0.  A snapshot is taken when the chain
+// holds af_lag updates past its root and its factors are adopted exactly af_lag accepts
+// later (waiting for them if need be), so the preconditioner sequence -- and every
+// result -- is independent of how fast the factor CTA runs.
+// ---------------------------------------------------------------------------
+
+// Thread 0: move the factor CTA's statistics into the solver's controller.
+__device__ void af_take_stats(Ctl* c, Ctl* sc) {
+  c->factorizations += sc->factorizations; sc->factorizations = 0;
+  c->cyc[PH_ILUTP] += sc->cyc[PH_ILUTP]; sc->cyc[PH_ILUTP] = 0;
+  c->cyc[PH_LEVELS] += sc->cyc[PH_LEVELS]; sc->cyc[PH_LEVELS] = 0;
+  c->af_factor_cyc += sc->cyc[PH_FACTOR]; sc->cyc[PH_FACTOR] = 0;
+  c->ilu_rows += sc->ilu_rows; sc->ilu_rows = 0;
+  c->ilu_elims += sc->ilu_elims; sc->ilu_elims = 0;
+  c->ilu_cand += sc->ilu_cand; sc->ilu_cand = 0;
+}
+
+// Block-wide: adopt factor set af_target and keep the chain entries s0 .. n_upd - 1
+// (moved to 0 .. n_upd - 1 - s0; G[s][t] = u_s^T z_hat_t does not depend on the root).
+template <typename T>
+__device__ void af_swap(const Walker& w0, Shared& sh) {
+  Ctl* c = w0.ctl;
+  const Ctl* sc = w0.shadow;
+  const int tid = threadIdx.x, nt = blockDim.x, n = w0.n;
+  const int s0 = c->af_snap, len = c->n_upd - s0;
+  T* Zt = (T*)w0.upd_z;
+  const int mcap = w0.mu4;
+  for (int i = tid; i < n; i += nt) {
+    T* zr = Zt + (size_t)i * mcap;
+    for (int j = 0; j < len; ++j) zr[j] = zr[s0 + j];
+  }
+  T* Uv = (T*)w0.upd_uval;
+  for (int j = 0; j < len; ++j) {  // destination rows in increasing order: sources are intact
+    const int ul = w0.upd_ulen[s0 + j];
+    for (int t = tid; t < ul; t += nt) {
+      w0.upd_ucol[(size_t)j * kMaxU + t] = w0.upd_ucol[(size_t)(s0 + j) * kMaxU + t];
+      Uv[(size_t)j * kMaxU + t] = Uv[(size_t)(s0 + j) * kMaxU + t];
+    }
+    for (int t = tid; t < j; t += nt) w0.upd_G[(size_t)j * kMaxUpd + t] = w0.upd_G[(size_t)(s0 + j) * kMaxUpd + s0 + t];
+    __syncthreads();
+    if (tid == 0) w0.upd_ulen[j] = ul;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int nnzu = 0;
+    for (int j = 0; j < len; ++j) nnzu += w0.upd_ulen[j];
+    c->upd_nnz = nnzu;
+    c->n_upd = len;
+    c->nlev_l = sc->nlev_l; c->nlev_u = sc->nlev_u;
+    c->nchunk_l = sc->nchunk_l; c->nchunk_u = sc->nchunk_u;
+    c->nnz_LU = sc->nnz_LU; c->nnz_A = sc->nnz_A;
+    c->p_lfil = sc->p_lfil; c->last_pivots = sc->last_pivots; c->last_breakdown = 0;
+    c->active = c->af_target;
+    c->refactors_async += 1;
+    st_release(&c->af_state, 0);
+  }
+  fence_proxy_async_global();  // the new streams are read by bulk copies next
+  __syncthreads();
+}
+
+// Block-wide, before every step of the solver CTA: adopt finished factors when the
+// chain has reached snapshot + af_lag, and request the next factorisation.
+template <typename T>
+__device__ __noinline__ void af_step_begin(const Walker& w0, const Params& P, Shared& sh) {
+  Ctl* c = w0.ctl;
+  if (threadIdx.x == 0) {
+    int act = 0;  // 1 adopt, 2 reorder + refactor now (the background one broke down)
+    const long long t0 = clock64();
+    int st = ld_acquire(&c->af_state);
+    const int nu = c->n_upd;
+    if (st != 0 && c->af_epoch_req != c->af_epoch) {
+      // stale: a synchronous factorisation came after the snapshot; wait for it (only
+      // when a new request is due, so that the request point stays fixed) and drop it
+      if (st == 1 && nu >= P.af_lag) st = wait_state_change(&c->af_state, 1);
+      if (st == 2) {
+        af_take_stats(c, w0.shadow);
+        st_release(&c->af_state, 0);
+      }
+    } else if (st != 0 && nu >= c->af_snap + P.af_lag) {
+      if (st == 1) st = wait_state_change(&c->af_state, 1);
+      if (st == 2) {
+        af_take_stats(c, w0.shadow);
+        const int fl = c->af_fail;
+        if (fl & 2) {
+          c->status = ST_CAPACITY;
+          st_release(&c->af_state, 0);
+        } else if (fl & 1) {
+          act = 2;
+          st_release(&c->af_state, 0);
+        } else {
+          act = 1;
+        }
+      }
+    }
+    if (st < 0 && c->status == ST_OK) c->status = ST_TIMEOUT;
+    c->af_wait_cyc += clock64() - t0;
+    sh.iflag[4] = act;
+  }
+  __syncthreads();
+  const int act = sh.iflag[4];
+  if (act == 1) {
+    fence_acq_rel_gpu();
+    af_swap<T>(w0, sh);
+  } else if (act == 2) {
+    const int fl = factor_block<T>(active_of(w0), P, sh, true);
+    if (threadIdx.x == 0) {
+      c->reorders += 1;
+      c->reorder_breakdown += 1;
+      if (fl & 2) c->status = ST_CAPACITY;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    sh.iflag[7] = (c->status == ST_OK && ld_acquire(&c->af_state) == 0 && c->n_upd >= P.af_lag) ? 1 : 0;
+  __syncthreads();
+  if (sh.iflag[7]) {
+    const int n = w0.n, tid = threadIdx.x, nt = blockDim.x;
+    for (size_t idx = tid; idx < (size_t)n * w0.cap; idx += nt) {
+      w0.snap_col[idx] = w0.a_col[idx];
+      w0.snap_val[idx] = w0.a_val[idx];
+    }
+    for (int p = tid; p < n; p += nt) {
+      w0.snap_len[p] = w0.a_len[p];
+      w0.snap_part[p] = w0.part_of_row[p];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      c->af_snap = c->n_upd;
+      c->af_epoch_req = c->af_epoch;
+      c->af_target = 1 - c->active;
+      __threadfence();
+      st_release(&c->af_state, 1);
+    }
+  }
+  __syncthreads();
+}
+
+// Thread 0 of the solver CTA, at the end of a launch: let the factor CTA finish the
+// request in flight, then tell it to leave.
+__device__ void af_finish(const Walker& w0, int launch_id) {
+  Ctl* c = w0.ctl;
+  int st = ld_acquire(&c->af_state);
+  if (st == 1) st = wait_state_change(&c->af_state, 1);
+  if (st < 0 && c->status == ST_OK) c->status = ST_TIMEOUT;
+  st_release(&c->af_stop, launch_id);
+}
+
+// The factor CTA: serve requests until the solver CTA marks the end of the launch.
+template <typename T>
+__device__ __noinline__ void af_factor_loop(const Walker& w0, const Params& P, int launch_id, Shared& sh) {
+  Ctl* c = w0.ctl;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int r = 3;  // 1 work, 2 stop, 3 gave up waiting
+      const unsigned long long t0 = global_ns();
+      for (;;) {
+        if (ld_acquire(&c->af_state) == 1) { r = 1; break; }
+        if (ld_acquire(&c->af_stop) == launch_id) { r = 2; break; }
+        if (global_ns() - t0 > kPairWaitNs) break;
+        __nanosleep(2000);
+      }
+      sh.iflag[5] = r;
+      sh.iflag[6] = r == 1 ? c->af_target : 0;
+    }
+    __syncthreads();
+    if (sh.iflag[5] != 1) break;  // the solver's own bounded waits report a lost partner
+    fence_acq_rel_gpu();
+    const Walker& wf = *w0.fact[sh.iflag[6]];
+    const int fl = factor_block<T>(wf, P, sh, false);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      c->af_fail = fl & 3;
+      __threadfence();
+      st_release(&c->af_state, 2);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -192,7 +377,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_sweep(const Walker* __restrict_
   __shared__ Shared sh;
   ring_init(sh, P);
   const int wi = walker0 + blockIdx.x;
-  const Walker& w = W[wi];
+  const Walker& w = active_of(W[wi]);
   const uint64_t seed = seeds[wi];
   const int n = w.n;
   for (int s = 0; s < n_sweeps; ++s)
@@ -203,6 +388,35 @@ __global__ void __launch_bounds__(kMaxThreads) k_sweep(const Walker* __restrict_
     }
 }
 
+// Persistent sweeps with background refactorisation: a cluster of two CTAs per walker,
+// rank 0 steps (as k_sweep), rank 1 factors (af_factor_loop).  launch_id: unique per
+// launch of this context, > 0.
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) k_sweep_pair(const Walker* __restrict__ W, int walker0, Params P,
+                                                     int n_sweeps, long long sweep0, double sigma,
+                                                     const uint64_t* __restrict__ seeds, uint8_t* acc_log,
+                                                     double* ratio_log, int launch_id) {
+  __shared__ Shared sh;
+  ring_init(sh, P);
+  const int wi = walker0 + (int)(blockIdx.x >> 1);
+  const Walker& w0 = W[wi];
+  if (blockIdx.x & 1) {
+    af_factor_loop<T>(w0, P, launch_id, sh);
+    return;
+  }
+  const uint64_t seed = seeds[wi];
+  const int n = w0.n;
+  for (int s = 0; s < n_sweeps; ++s)
+    for (int k = 0; k < n; ++k) {
+      af_step_begin<T>(w0, P, sh);
+      const Walker& w = active_of(w0);
+      const long long idx = (long long)n_sweeps * w.log_base + (long long)s * n + k;
+      mc_step<T>(w, P, k, seed, (uint32_t)(sweep0 + s), sigma, acc_log ? acc_log + idx : nullptr,
+                 ratio_log ? ratio_log + idx : nullptr, sh);
+    }
+  if (threadIdx.x == 0) af_finish(w0, launch_id);
+}
+
 // One step (particle q of sweep s_local of a batch of n_sweeps) for every walker in the grid.
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_step(const Walker* __restrict__ W, int walker0, Params P, int q, int n_sweeps,
@@ -210,7 +424,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_step(const Walker* __restrict__
                                                const uint64_t* __restrict__ seeds, uint8_t* acc_log, double* ratio_log) {
   __shared__ Shared sh;
   const int wi = walker0 + blockIdx.x;
-  const Walker& w = W[wi];
+  const Walker& w = active_of(W[wi]);
   if (q >= w.n) return;
   ring_init(sh, P);
   const long long idx = (long long)n_sweeps * w.log_base + (long long)s_local * w.n + q;
@@ -224,7 +438,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_ratio(const Walker* __restrict_
                                                 double ry, double rz) {
   __shared__ Shared sh;
   ring_init(sh, P);
-  const Walker& w = W[wi];
+  const Walker& w = active_of(W[wi]);
   Ctl* c = w.ctl;
   if (threadIdx.x == 0) {
     sh.rnew[0] = wrap_box(rx, w.L);
@@ -253,7 +467,7 @@ template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_accept(const Walker* __restrict__ W, int wi, Params P) {
   __shared__ Shared sh;
   ring_init(sh, P);
-  const Walker& w = W[wi];
+  const Walker& w = active_of(W[wi]);
   Ctl* c = w.ctl;
   const int valid = c->pend_valid;
   const int k = c->pend_k;
@@ -287,7 +501,7 @@ template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_setup(const Walker* __restrict__ W, int walker0, Params P) {
   __shared__ Shared sh;
   ring_init(sh, P);
-  const Walker& w = W[walker0 + blockIdx.x];
+  const Walker& w = active_of(W[walker0 + blockIdx.x]);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   Ctl* c = w.ctl;
   int bad = 0;
@@ -321,7 +535,7 @@ template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_refactor(const Walker* __restrict__ W, int wi, Params P, int reorder) {
   __shared__ Shared sh;
   ring_init(sh, P);
-  const Walker& w = W[wi];
+  const Walker& w = active_of(W[wi]);
   factor_block<T>(w, P, sh, reorder != 0);
 }
 
@@ -329,7 +543,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_refactor(const Walker* __restri
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_apply_precond(const Walker* __restrict__ W, int wi, Params P) {
   __shared__ Shared sh;
-  const Walker& w = W[wi];
+  const Walker& w = active_of(W[wi]);
   ring_init(sh, P);
   T* V = (T*)w.V;
   T* Zk = (T*)w.Zk;
@@ -346,7 +560,7 @@ template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_bench(const Walker* __restrict__ W, Params P, int which, int reps) {
   __shared__ Shared sh;
   ring_init(sh, P);
-  const Walker& w = W[blockIdx.x];
+  const Walker& w = active_of(W[blockIdx.x]);
   const int n = w.n;
   T* V = (T*)w.V;
   T* Zk = (T*)w.Zk;
@@ -355,10 +569,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_bench(const Walker* __restrict_
   T* y = P.y_smem ? (T*)dyn_smem() : (T*)w.tv;
   for (int it = 0; it < reps; ++it) {
     if (which == 0) {
+      const long long t0 = clock64();
       for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = V[i];
       __syncthreads();
       tri_staged<T>(w, P, false, y, sh);
       tri_staged<T>(w, P, true, y, sh);
+      if (threadIdx.x == 0) w.ctl->cyc[PH_TRI] += clock64() - t0;
       for (int i = threadIdx.x; i < n; i += blockDim.x) Zk[w.perm[i]] = y[i];
       if (threadIdx.x == 0)
         w.ctl->alg_bytes += w.ctl->nnz_LU * (sizeof(T) + 4) + (double)n * (3 * sizeof(T) + 8);
@@ -422,6 +638,32 @@ cudaError_t launch_sweep(const LaunchCfg& L, const Walker* W, int walker0, int n
                          long long sweep0, double sigma, const uint64_t* seeds, uint8_t* acc, double* ratio) {
   if (L.fp64) VMC_LAUNCH(k_sweep<double>, nwalk, W, walker0, P, n_sweeps, sweep0, sigma, seeds, acc, ratio);
   VMC_LAUNCH(k_sweep<float>, nwalk, W, walker0, P, n_sweeps, sweep0, sigma, seeds, acc, ratio);
+}
+cudaError_t launch_sweep_pair(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P,
+                              int n_sweeps, long long sweep0, double sigma, const uint64_t* seeds, uint8_t* acc,
+                              double* ratio, int launch_id) {
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(2 * nwalk);
+  lc.blockDim = dim3(L.threads);
+  lc.dynamicSmemBytes = L.smem;
+  lc.stream = L.stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  if (L.fp64) {
+    cudaError_t e = prep(k_sweep_pair<double>, L);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&lc, k_sweep_pair<double>, W, walker0, P, n_sweeps, sweep0, sigma, seeds, acc, ratio,
+                              launch_id);
+  }
+  cudaError_t e = prep(k_sweep_pair<float>, L);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchKernelEx(&lc, k_sweep_pair<float>, W, walker0, P, n_sweeps, sweep0, sigma, seeds, acc, ratio,
+                            launch_id);
 }
 cudaError_t launch_step(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int q,
                         int n_sweeps, int s_local, long long sweep0, double sigma, const uint64_t* seeds,

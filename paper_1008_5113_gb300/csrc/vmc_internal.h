@@ -21,6 +21,10 @@ int kernel_static_smem(bool fp64);
 
 cudaError_t launch_sweep(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int n_sweeps,
                          long long sweep0, double sigma, const uint64_t* seeds, uint8_t* acc, double* ratio);
+// Persistent sweeps with a factor CTA per walker (cluster of 2); see k_sweep_pair.
+cudaError_t launch_sweep_pair(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P,
+                              int n_sweeps, long long sweep0, double sigma, const uint64_t* seeds, uint8_t* acc,
+                              double* ratio, int launch_id);
 cudaError_t launch_step(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int q,
                         int n_sweeps, int s_local, long long sweep0, double sigma, const uint64_t* seeds,
                         uint8_t* acc, double* ratio);

@@ -136,8 +136,11 @@ __device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, boo
   } else {
     int slot = seq0 % S;
     unsigned parity = (unsigned)((seq0 / S) & 1);
+    long long tdata = 0;
     for (int c = 0; c < nch; ++c) {
+      const long long tw0 = clock64();
       if (!mbar_wait(&sh.bar[slot], parity)) sh.iflag[3] = 1;
+      tdata += clock64() - tw0;
       const unsigned char* ch = ring + (size_t)slot * SB;
       const int4 hd = *(const int4*)ch;
       const int nseg = hd.x, nr = hd.y, ne = hd.z;
@@ -182,12 +185,11 @@ __device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, boo
       if (tid == 0) mbar_arrive(&sh.ebar[slot]);
       if (++slot == S) { slot = 0; parity ^= 1u; }
     }
+    if (tid == 0) w.ctl->cyc[PH_TRIDATA] += tdata;
   }
+  if (wid == nwarp - 1 && lane == 0) w.ctl->cyc[PH_TRIWAIT] += twait;
   __syncthreads();
-  if (tid == 0) {
-    sh.ring_seq = seq0 + nch;
-    w.ctl->cyc[PH_TRIWAIT] += twait;
-  }
+  if (tid == 0) sh.ring_seq = seq0 + nch;
   __syncthreads();
 }
 

@@ -90,7 +90,7 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   if (params) p = *params;
   else vmc_default_params(&p);
   if (p.gmres_m < 1 || p.gmres_m > kMaxM || p.max_updates < 0 || p.max_updates > kMaxUpd ||
-      (p.precision != VMC_PREC_FP64 && p.precision != VMC_PREC_MIXED) ||
+      (p.precision != VMC_PREC_FP64 && p.precision != VMC_PREC_MIXED && p.precision != VMC_PREC_MIXED_F32ILU) ||
       (p.block_threads != 0 && (p.block_threads < 64 || p.block_threads > kMaxThreads || p.block_threads % 32)) ||
       !(p.drop_tol >= 0.0) || !(p.permtol >= 0.0) || p.max_restarts < 0)
     return fail(VMC_ERR_INVALID, "invalid solver parameters");
@@ -175,6 +175,7 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   P.max_restarts = p.max_restarts; P.max_updates = p.max_updates;
   P.inner_rtol = p.inner_rtol > 0.0 ? p.inner_rtol : (fp64 ? 1e-10 : 1e-5);
   P.ratio_tol = p.ratio_tol > 0.0 ? p.ratio_tol : 1e-12;
+  P.ilu64 = p.precision != VMC_PREC_MIXED_F32ILU;
   P.N_max = p.N_max; P.slow_factor = p.slow_factor;
   // shared-memory plan for a single walker CTA
   int dev = 0, optin = 0;

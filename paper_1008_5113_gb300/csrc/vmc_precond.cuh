@@ -715,7 +715,7 @@ __device__ __noinline__ int factor_block(const Walker& w, const Params& P, Share
     double nnz = 0.0;
     for (int r = threadIdx.x; r < w.n; r += 32) w.lev_u[r] = 0;
     const long long ti = clock64();
-    const int fl = ilutp_warp<T>(w, P, sh, &npiv, &nnz, &p);
+    const int fl = P.ilu64 ? ilutp_warp<double>(w, P, sh, &npiv, &nnz, &p) : ilutp_warp<T>(w, P, sh, &npiv, &nnz, &p);
     if (threadIdx.x == 0) w.ctl->cyc[PH_ILUTP] += clock64() - ti;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // scratch is reused by bulk copies
     if (threadIdx.x == 0) {
@@ -728,6 +728,7 @@ __device__ __noinline__ int factor_block(const Walker& w, const Params& P, Share
       c->n_upd = 0;
       c->upd_nnz = 0;
       c->last_breakdown = fl & 1;
+      c->af_epoch += 1;  // a background factorisation requested before this one is stale
     }
   }
   __syncthreads();

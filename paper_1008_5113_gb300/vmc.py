@@ -23,7 +23,7 @@ _lib = None
 
 STATUS = {0: "VMC_OK", 1: "VMC_ERR_INVALID", 2: "VMC_ERR_CUDA", 3: "VMC_ERR_OOM", 4: "VMC_ERR_NOCONV",
           5: "VMC_ERR_BREAKDOWN", 6: "VMC_ERR_TIMEOUT", 7: "VMC_ERR_STATE", 8: "VMC_ERR_CAPACITY"}
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_MIXED_F32ILU = 0, 1, 2
 ENGINE_PLAIN, ENGINE_STEP, ENGINE_PERSISTENT, ENGINE_DENSE_SM = 0, 1, 2, 3
 
 
@@ -43,7 +43,7 @@ class vmc_solver_params(C.Structure):
                 ("gmres_m", C.c_int), ("max_restarts", C.c_int), ("inner_rtol", C.c_double),
                 ("ratio_tol", C.c_double), ("N_max", C.c_double), ("slow_factor", C.c_double),
                 ("max_updates", C.c_int), ("precision", C.c_int), ("engine", C.c_int),
-                ("block_threads", C.c_int), ("sm_refresh", C.c_int)]
+                ("block_threads", C.c_int), ("sm_refresh", C.c_int), ("refactor_lag", C.c_int)]
 
 
 class vmc_stats(C.Structure):
@@ -56,7 +56,9 @@ class vmc_stats(C.Structure):
                 ("levels_L", C.c_int), ("levels_U", C.c_int), ("n_updates", C.c_int), ("status", C.c_int),
                 ("its_hist", C.c_int64 * 64), ("phase_cycles", C.c_int64 * 16), ("alg_bytes", C.c_double),
                 ("ilu_rows", C.c_int64), ("ilu_elims", C.c_int64), ("ilu_cand", C.c_int64),
-                ("chunks_L", C.c_int), ("chunks_U", C.c_int)]
+                ("chunks_L", C.c_int), ("chunks_U", C.c_int), ("refactors_async", C.c_int64),
+                ("async_wait_cycles", C.c_int64), ("async_factor_cycles", C.c_int64), ("factor_set", C.c_int),
+                ("async_lag", C.c_int)]
 
 
 # name -> (restype, argtypes); every symbol the header declares

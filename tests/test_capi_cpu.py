@@ -72,3 +72,30 @@ def test_null_arguments(vmc):
     assert lib.vmc_default_params(None) == 1
     assert lib.vmc_destroy(None) == 1
     assert lib.vmc_philox_device(None, None, None, 0) == 1
+
+
+def test_struct_layouts_match_the_header(vmc, tmp_path):
+    """The binding's ctypes structures have the C compiler's sizes and offsets."""
+    import shutil
+    import subprocess
+
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = {"vmc_system": vmc.vmc_system, "vmc_solver_params": vmc.vmc_solver_params,
+               "vmc_stats": vmc.vmc_stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "vmc.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.split("\n") if l)
+    for name, cls in structs.items():
+        assert int(out[name]) == C.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(out[f"{name}.{field}"]) == getattr(cls, field).offset, f"{name}.{field}"

@@ -97,10 +97,11 @@ def test_plain_216_chain_matches_oracle(vmc, prec):
 
 
 def test_engines_agree_bitwise(vmc):
+    """With in-line refactorisation the three launch shapes run the same arithmetic."""
     wl = WL.PLAIN_216
     logs = {}
     for eng in (vmc.ENGINE_PERSISTENT, vmc.ENGINE_STEP, vmc.ENGINE_PLAIN):
-        ctx = vmc.vmc_create(wl.systems() * 2, vmc.params(precision=0, engine=eng))
+        ctx = vmc.vmc_create(wl.systems() * 2, vmc.params(precision=0, engine=eng, refactor_lag=0))
         try:
             vmc.vmc_init_positions(ctx, [1, 2], wl.jitter)
             logs[eng] = vmc.vmc_sweep(ctx, 1, wl.sigma, [1, 2])
