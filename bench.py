@@ -198,6 +198,13 @@ def main():
         vmc.vmc_init_positions(ctx, seeds[:nw], JITTER)
         return ctx
 
+    def refactor_mode(ctx):
+        lag = vmc.vmc_get_stats(ctx, 0)["async_lag"]
+        if lag > 0:
+            return (f"background: a factor CTA per walker (cluster of 2) refactors a snapshot, adopted "
+                    f"{lag} accepts later")
+        return "in line, when the update chain is full"
+
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     seeds_dev = torch.tensor(seeds, dtype=torch.int64, device="cuda")
 
@@ -224,6 +231,8 @@ def main():
 
     # ---- headline: batched FP64, persistent engine (one launch per sweep) ------------
     ctx = make(vmc.PREC_FP64, vmc.ENGINE_PERSISTENT)
+    refactoring = refactor_mode(ctx)
+    kernel_name = "k_sweep_pair" if vmc.vmc_get_stats(ctx, 0)["async_lag"] > 0 else "k_sweep"
     with Clocks(dev) as clk:
         total_ms, per_ms, wall = timed_sweeps(ctx, args.steps, args.warmup)
     stats = [vmc.vmc_get_stats(ctx, w) for w in range(WALKERS)]
@@ -280,7 +289,7 @@ def main():
         return
 
     hbm, peak_kind = peaks()
-    kernel_ms = total_ms / args.steps        # one k_sweep launch per step
+    kernel_ms = total_ms / args.steps        # one sweep launch per step
     achieved = alg_bytes / args.steps / (kernel_ms / 1000.0) / 1e9
     its = sum(s["inner_iterations"] for s in stats) / ratios_local
     out = {
@@ -289,7 +298,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N, "walkers_per_gpu": WALKERS, "sweeps_per_step": 1,
                    "engine": "persistent (one launch per sweep, CTA per walker)", "gmres_m": 30,
-                   "ilutp": "drop 1e-4, permtol 0.5", "inner_rtol": 1e-10,
+                   "ilutp": "drop 1e-4, permtol 0.5", "inner_rtol": 1e-10, "refactorisation": refactoring,
                    "l2": "256 MB buffer written between timed steps"},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
@@ -297,7 +306,8 @@ def main():
                 "d2h_bytes_per_step": 9 * WALKERS * N},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
-                     "note": f"k_sweep, algorithmic bytes from the kernel's per-phase counter; peak {peak_kind}"},
+                     "note": f"{kernel_name}, algorithmic bytes from the kernel's per-phase counter; peak "
+                             f"{peak_kind}"},
         "solver": {"inner_its_per_ratio": its,
                    "accept_rate": sum(s["accepts"] for s in stats) / ratios_local,
                    "reorders": sum(s["reorders"] for s in stats),

@@ -91,7 +91,7 @@ typedef struct {
   int max_updates;     /* refactor after this many rank-one preconditioner updates (64)   */
   int precision;       /* VMC_PREC_* (MIXED)                                               */
   int engine;          /* VMC_ENGINE_* (PERSISTENT)                                        */
-  int block_threads;   /* threads per walker CTA: 64..512, multiple of 32; 0 = auto (0)  */
+  int block_threads;   /* threads per walker CTA: 64..256, multiple of 32; 0 = auto (0)  */
   int sm_refresh;      /* dense engine: fresh inverse every sm_refresh sweeps; 0: never (1) */
   int refactor_lag;    /* PERSISTENT engine: background refactorisation.  A second CTA per
                           walker (a cluster of two) factors a snapshot of A taken once the
@@ -102,6 +102,13 @@ typedef struct {
                           0: off (refactor in line when the chain is full); > 0: on, clamped
                           to max_updates / 2; -1: auto -- on with max_updates / 2 when every
                           walker pair fits on the GPU at once (2 x walkers <= SMs) (-1) */
+  int refactor_reorder; /* background refactorisations first re-pair particles and orbitals
+                          (the greedy reordering of Sec. 3.1) on the snapshot positions; the
+                          solver adopts the new row order with the factors (0) */
+  int trisolve;        /* triangular solves: 0 = level-synchronous (a barrier per level, the
+                          next level's rows gathered ahead of it); 1 = synchronisation-free
+                          when both solve vectors fit in shared memory (a warp waits only for
+                          the entries its rows read), else level-synchronous (0) */
 } vmc_solver_params;
 
 /* Per-walker statistics (Sec. 4 Tables 2 and 3 analogues). */

@@ -20,9 +20,17 @@ using namespace vmc;
 // ---------------------------------------------------------------------------
 namespace vmc {
 
-void plan_smem(int ybytes, int budget, Params& P) {
+void plan_smem(int ybytes, int budget, Params& P, bool allow_sf) {
   int avail = budget;
-  if (ybytes + 2 * kSlotBytes <= budget) {
+  P.tri_sf = 0;
+  P.y_half = 0;
+  if (allow_sf && 2 * ybytes + 4 * kSlotBytes <= budget) {
+    P.tri_sf = 1;  // both solve vectors in shared memory: synchronisation-free solves
+    P.y_smem = 1;
+    P.y_bytes = 2 * ybytes;
+    P.y_half = ybytes;
+    avail = budget - 2 * ybytes;
+  } else if (ybytes + 2 * kSlotBytes <= budget) {
     P.y_smem = 1;
     P.y_bytes = ybytes;
     avail = budget - ybytes;
@@ -175,6 +183,8 @@ extern "C" vmc_status vmc_default_params(vmc_solver_params* p) {
   p->block_threads = 0;
   p->sm_refresh = 1;
   p->refactor_lag = -1;
+  p->refactor_reorder = 0;
+  p->trisolve = 0;
   return VMC_OK;
 }
 
@@ -289,9 +299,10 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   else if (p.engine == VMC_ENGINE_DENSE_SM && p.precision != VMC_PREC_FP64) st = bad("the dense engine is FP64 only");
   else if (p.sm_refresh < 0) st = bad("sm_refresh must be >= 0");
   else if (p.block_threads != 0 && (p.block_threads < 64 || p.block_threads > kMaxThreads || p.block_threads % 32))
-    st = bad("block_threads must be 0 or a multiple of 32 in [64, 512]");
+    st = bad("block_threads must be 0 or a multiple of 32 in [64, 256]");
   else if (!(p.drop_tol >= 0.0) || !(p.permtol >= 0.0) || p.max_restarts < 0) st = bad("ILUTP/GMRES parameters");
   else if (p.refactor_lag < -1) st = bad("refactor_lag must be >= -1");
+  else if (p.trisolve < 0 || p.trisolve > 1) st = bad("trisolve must be 0 or 1");
   if (st != VMC_OK) { *out = ctx; return st; }
   ctx->fp64 = p.precision == VMC_PREC_FP64;
   ctx->threads = p.block_threads ? p.block_threads : 256;
@@ -316,6 +327,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     lag = std::min(lag, p.max_updates / 2);
     if (p.engine != VMC_ENGINE_PERSISTENT) lag = 0;
     ctx->P.af_lag = std::max(lag, 0);
+    ctx->P.af_reorder = p.refactor_reorder ? 1 : 0;
     ctx->pair = ctx->P.af_lag > 0;
   }
 
@@ -433,6 +445,10 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
       o.push_back(cv.take<int>((size_t)n * cap));      // 75 snap_col
       o.push_back(cv.take<double>((size_t)n * cap));   // 76 snap_val
       o.push_back(cv.take<int>(n));                    // 77 snap_part
+      o.push_back(cv.take<double>((size_t)n * 3));     // 78 snap_R
+      o.push_back(cv.take<int>(n));                    // 79 snap_rop
+      o.push_back(cv.take<int>(n));                    // 80 gP of the factor CTA
+      o.push_back(cv.take<int>(n));                    // 81 gQ of the factor CTA
     }
     Walker& W = ctx->hw[w];
     std::memset(&W, 0, sizeof(W));
@@ -463,7 +479,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     const int budget2 = per_sm / 2 - 1024 - stat;
     int budget = budget1;
     if (n_walkers > nsm && budget2 >= ybytes + 2 * kSlotBytes) budget = budget2;
-    plan_smem(ybytes, budget, ctx->P);
+    plan_smem(ybytes, budget, ctx->P, p.trisolve == 1);
     ctx->smem = (size_t)ctx->P.dsm_bytes;
   }
   const size_t ctl_off = cv.take<Ctl>(n_walkers);
@@ -583,6 +599,8 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
       W0.snap_col = (int*)(A + o[75]);
       W0.snap_val = (double*)(A + o[76]);
       W0.snap_part = (int*)(A + o[77]);
+      W0.snap_R = (double*)(A + o[78]);
+      W0.snap_rop = (int*)(A + o[79]);
       W0.shadow = ctx->dShadow + w;
       W0.set_id = 0;
       W1.set_id = 1;
@@ -592,6 +610,10 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
         F.a_val = W0.snap_val;
         F.a_len = W0.snap_len;
         F.part_of_row = W0.snap_part;
+        F.row_of_part = W0.snap_rop;
+        F.R = W0.snap_R;
+        F.gP = (int*)(A + o[80]);
+        F.gQ = (int*)(A + o[81]);
         F.ctl = W0.shadow;
         F.alt = nullptr;
         F.fact[0] = F.fact[1] = nullptr;
@@ -604,6 +626,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
       W1.fact[0] = W0.fact[0];
       W1.fact[1] = W0.fact[1];
       W1.snap_len = W0.snap_len; W1.snap_col = W0.snap_col; W1.snap_val = W0.snap_val; W1.snap_part = W0.snap_part;
+      W1.snap_R = W0.snap_R; W1.snap_rop = W0.snap_rop;
       W1.shadow = W0.shadow;
     }
     e = cudaMemcpyAsync(ctx->dW1, ctx->hw1.data(), sizeof(Walker) * n_walkers, cudaMemcpyHostToDevice, ctx->stream);

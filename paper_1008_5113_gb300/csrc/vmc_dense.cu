@@ -135,7 +135,7 @@ __device__ void dense_step(const Walker& w, int k, uint64_t seed, uint32_t sweep
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kMaxThreads) k_dense_setup(const Walker* __restrict__ W) {
+__global__ void __launch_bounds__(kMaxThreads, 2) k_dense_setup(const Walker* __restrict__ W) {
   __shared__ Shared sh;
   const Walker& w = W[blockIdx.x];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_dense_setup(const Walker* __res
   }
 }
 
-__global__ void __launch_bounds__(kMaxThreads) k_dense_sweep(const Walker* __restrict__ W, int n_sweeps, long long sweep0,
+__global__ void __launch_bounds__(kMaxThreads, 2) k_dense_sweep(const Walker* __restrict__ W, int n_sweeps, long long sweep0,
                                                              double sigma, const uint64_t* __restrict__ seeds,
                                                              uint8_t* acc_log, double* ratio_log, int refresh) {
   __shared__ Shared sh;

@@ -22,7 +22,7 @@
 
 namespace vmc {
 
-constexpr int kMaxThreads = 512;  // largest walker CTA
+constexpr int kMaxThreads = 256;  // largest walker CTA (two per SM with up to 128 registers a thread)
 constexpr int kMaxM = 40;         // largest Krylov dimension
 constexpr int kMaxRow = 256;      // largest Slater row (entries)
 constexpr int kMaxU = 2 * kMaxRow;
@@ -125,6 +125,7 @@ struct Walker {
   const Walker* fact[2];
   int set_id;
   int* snap_len; int* snap_col; double* snap_val; int* snap_part;
+  double* snap_R; int* snap_rop;  // positions and row-of-particle at the snapshot
   Ctl* shadow;
 };
 
@@ -144,6 +145,9 @@ struct Params {
   int dsm_bytes;    // total dynamic shared memory (ILUTP scratch may use all of it)
   int ilu64;        // 1: the ILUTP working row is FP64 whatever the stored precision
   int af_lag;       // background refactorisation: accepts between a snapshot and its use (0: off)
+  int af_reorder;   // 1: background refactorisations re-pair particles and orbitals first
+  int tri_sf;       // 1: synchronisation-free triangular solves (two solve vectors in shared memory)
+  int y_half;       // byte offset of the second solve vector (tri_sf)
 };
 
 // Shared memory of a walker CTA (static, < 48 KB).

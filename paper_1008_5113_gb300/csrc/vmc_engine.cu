@@ -188,7 +188,10 @@ __device__ __noinline__ void mc_step(const Walker& w, const Params& P, int k, ui
 // the update chain on the new factors.  With U_s = I - z_hat_s u_s^T the identity
 // A_{s+1} M_{s+1} = A_s M_s (Sec. 3.2 Eqs. 16-18) holds whatever M the chain starts
 // from, so after the swap the solver applies U_{m-1} ... U_{s0} (LU of A_{s0})^{-1} and
-// drops the updates older than the snapshot s0.  A snapshot is taken when the chain
+// drops the updates older than the snapshot s0.  The factor CTA may also re-pair
+// particles and orbitals first (greedy reordering, Sec. 3.1): a new row order P' leaves
+// x = A_p^{-1} e_{row(k)}, z_hat and u (column space) unchanged, so the chain carries
+// over to the re-paired root as well.  A snapshot is taken when the chain
 // holds af_lag updates past its root and its factors are adopted exactly af_lag accepts
 // later (waiting for them if need be), so the preconditioner sequence -- and every
 // result -- is independent of how fast the factor CTA runs.
@@ -208,7 +211,7 @@ __device__ void af_take_stats(Ctl* c, Ctl* sc) {
 // Block-wide: adopt factor set af_target and keep the chain entries s0 .. n_upd - 1
 // (moved to 0 .. n_upd - 1 - s0; G[s][t] = u_s^T z_hat_t does not depend on the root).
 template <typename T>
-__device__ void af_swap(const Walker& w0, Shared& sh) {
+__device__ void af_swap(const Walker& w0, const Params& P, Shared& sh) {
   Ctl* c = w0.ctl;
   const Ctl* sc = w0.shadow;
   const int tid = threadIdx.x, nt = blockDim.x, n = w0.n;
@@ -229,6 +232,14 @@ __device__ void af_swap(const Walker& w0, Shared& sh) {
     for (int t = tid; t < j; t += nt) w0.upd_G[(size_t)j * kMaxUpd + t] = w0.upd_G[(size_t)(s0 + j) * kMaxUpd + s0 + t];
     __syncthreads();
     if (tid == 0) w0.upd_ulen[j] = ul;
+  }
+  if (P.af_reorder) {
+    // the new row pairing comes with the factors; the chain lives in column space and
+    // x = A_p^{-1} e_{row(k)} does not depend on the row order, so it carries over
+    for (int r = tid; r < n; r += nt) {
+      w0.part_of_row[r] = w0.snap_part[r];
+      w0.row_of_part[r] = w0.snap_rop[r];
+    }
   }
   __syncthreads();
   if (tid == 0) {
@@ -290,7 +301,7 @@ __device__ __noinline__ void af_step_begin(const Walker& w0, const Params& P, Sh
   const int act = sh.iflag[4];
   if (act == 1) {
     fence_acq_rel_gpu();
-    af_swap<T>(w0, sh);
+    af_swap<T>(w0, P, sh);
   } else if (act == 2) {
     const int fl = factor_block<T>(active_of(w0), P, sh, true);
     if (threadIdx.x == 0) {
@@ -313,6 +324,8 @@ __device__ __noinline__ void af_step_begin(const Walker& w0, const Params& P, Sh
       w0.snap_len[p] = w0.a_len[p];
       w0.snap_part[p] = w0.part_of_row[p];
     }
+    if (P.af_reorder)
+      for (int i = tid; i < 3 * n; i += nt) w0.snap_R[i] = w0.R[i];
     __syncthreads();
     if (tid == 0) {
       c->af_snap = c->n_upd;
@@ -356,7 +369,7 @@ __device__ __noinline__ void af_factor_loop(const Walker& w0, const Params& P, i
     if (sh.iflag[5] != 1) break;  // the solver's own bounded waits report a lost partner
     fence_acq_rel_gpu();
     const Walker& wf = *w0.fact[sh.iflag[6]];
-    const int fl = factor_block<T>(wf, P, sh, false);
+    const int fl = factor_block<T>(wf, P, sh, P.af_reorder != 0);
     __syncthreads();
     if (threadIdx.x == 0) {
       c->af_fail = fl & 3;
@@ -371,7 +384,7 @@ __device__ __noinline__ void af_factor_loop(const Walker& w0, const Params& P, i
 // kernels
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) k_sweep(const Walker* __restrict__ W, int walker0, Params P, int n_sweeps,
+__global__ void __launch_bounds__(kMaxThreads, 2) k_sweep(const Walker* __restrict__ W, int walker0, Params P, int n_sweeps,
                                                 long long sweep0, double sigma, const uint64_t* __restrict__ seeds,
                                                 uint8_t* acc_log, double* ratio_log) {
   __shared__ Shared sh;
@@ -392,7 +405,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_sweep(const Walker* __restrict_
 // rank 0 steps (as k_sweep), rank 1 factors (af_factor_loop).  launch_id: unique per
 // launch of this context, > 0.
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) k_sweep_pair(const Walker* __restrict__ W, int walker0, Params P,
+__global__ void __launch_bounds__(kMaxThreads, 2) k_sweep_pair(const Walker* __restrict__ W, int walker0, Params P,
                                                      int n_sweeps, long long sweep0, double sigma,
                                                      const uint64_t* __restrict__ seeds, uint8_t* acc_log,
                                                      double* ratio_log, int launch_id) {
@@ -419,7 +432,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_sweep_pair(const Walker* __rest
 
 // One step (particle q of sweep s_local of a batch of n_sweeps) for every walker in the grid.
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) k_step(const Walker* __restrict__ W, int walker0, Params P, int q, int n_sweeps,
+__global__ void __launch_bounds__(kMaxThreads, 2) k_step(const Walker* __restrict__ W, int walker0, Params P, int q, int n_sweeps,
                                                int s_local, long long sweep0, double sigma,
                                                const uint64_t* __restrict__ seeds, uint8_t* acc_log, double* ratio_log) {
   __shared__ Shared sh;
@@ -434,7 +447,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_step(const Walker* __restrict__
 
 // Single-move API: ratio for particle k moved to r_new (no commit); result in ctl.
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) k_ratio(const Walker* __restrict__ W, int wi, Params P, int k, double rx,
+__global__ void __launch_bounds__(kMaxThreads, 2) k_ratio(const Walker* __restrict__ W, int wi, Params P, int k, double rx,
                                                 double ry, double rz) {
   __shared__ Shared sh;
   ring_init(sh, P);
@@ -464,7 +477,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_ratio(const Walker* __restrict_
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) k_accept(const Walker* __restrict__ W, int wi, Params P) {
+__global__ void __launch_bounds__(kMaxThreads, 2) k_accept(const Walker* __restrict__ W, int wi, Params P) {
   __shared__ Shared sh;
   ring_init(sh, P);
   const Walker& w = active_of(W[wi]);
@@ -498,7 +511,7 @@ __global__ void k_init_positions(const Walker* __restrict__ W, const uint64_t* _
 // All Slater rows from the positions (warp per particle), then the initial pairing
 // (particle i with orbital i), the greedy reordering and the first factorisation.
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) k_setup(const Walker* __restrict__ W, int walker0, Params P) {
+__global__ void __launch_bounds__(kMaxThreads, 2) k_setup(const Walker* __restrict__ W, int walker0, Params P) {
   __shared__ Shared sh;
   ring_init(sh, P);
   const Walker& w = active_of(W[walker0 + blockIdx.x]);
@@ -532,7 +545,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_setup(const Walker* __restrict_
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) k_refactor(const Walker* __restrict__ W, int wi, Params P, int reorder) {
+__global__ void __launch_bounds__(kMaxThreads, 2) k_refactor(const Walker* __restrict__ W, int wi, Params P, int reorder) {
   __shared__ Shared sh;
   ring_init(sh, P);
   const Walker& w = active_of(W[wi]);
@@ -541,7 +554,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_refactor(const Walker* __restri
 
 // z = M v for the test entry point: v in r64 (FP64), result in x64 (FP64).
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) k_apply_precond(const Walker* __restrict__ W, int wi, Params P) {
+__global__ void __launch_bounds__(kMaxThreads, 2) k_apply_precond(const Walker* __restrict__ W, int wi, Params P) {
   __shared__ Shared sh;
   const Walker& w = active_of(W[wi]);
   ring_init(sh, P);
@@ -557,7 +570,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_apply_precond(const Walker* __r
 // (0: L and U triangular solves, 1: SpMV in the working precision, 2: the full
 // preconditioner apply with the update chain), on V[0] = 1 / sqrt(n).
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads) k_bench(const Walker* __restrict__ W, Params P, int which, int reps) {
+__global__ void __launch_bounds__(kMaxThreads, 2) k_bench(const Walker* __restrict__ W, Params P, int which, int reps) {
   __shared__ Shared sh;
   ring_init(sh, P);
   const Walker& w = active_of(W[blockIdx.x]);
@@ -566,14 +579,10 @@ __global__ void __launch_bounds__(kMaxThreads) k_bench(const Walker* __restrict_
   T* Zk = (T*)w.Zk;
   for (int i = threadIdx.x; i < n; i += blockDim.x) V[i] = (T)rsqrt((double)n);
   __syncthreads();
-  T* y = P.y_smem ? (T*)dyn_smem() : (T*)w.tv;
   for (int it = 0; it < reps; ++it) {
     if (which == 0) {
       const long long t0 = clock64();
-      for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = V[i];
-      __syncthreads();
-      tri_staged<T>(w, P, false, y, sh);
-      tri_staged<T>(w, P, true, y, sh);
+      const T* y = tri_both<T>(w, P, V, sh);
       if (threadIdx.x == 0) w.ctl->cyc[PH_TRI] += clock64() - t0;
       for (int i = threadIdx.x; i < n; i += blockDim.x) Zk[w.perm[i]] = y[i];
       if (threadIdx.x == 0)

@@ -41,10 +41,12 @@ cudaError_t launch_dense_sweep(const LaunchCfg& L, const Walker* W, int nwalk, i
 cudaError_t launch_wait_timeout(int* status, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, cudaStream_t s);
 
-// Shared-memory plan of a walker CTA: the solve vector (ybytes) in shared memory when
-// it fits next to a ring of >= 2 slots; 16 KB slots when at least four fit, else 8 KB.
-// Fills y_smem, y_bytes, ring_slots, slot_bytes, dsm_bytes.
-void plan_smem(int ybytes, int budget, Params& P);
+// Shared-memory plan of a walker CTA: two solve vectors (2 ybytes) in shared memory
+// when they fit next to four ring slots and allow_sf (synchronisation-free triangular
+// solves), else one when it fits next to two slots, else none; then 16 KB slots when at
+// least four fit, else 8 KB.  Fills tri_sf, y_half, y_smem, y_bytes, ring_slots,
+// slot_bytes, dsm_bytes.
+void plan_smem(int ybytes, int budget, Params& P, bool allow_sf);
 
 // host-side geometry and layout
 struct Layout {

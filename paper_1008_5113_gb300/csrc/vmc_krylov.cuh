@@ -82,9 +82,12 @@ __device__ __forceinline__ void spmv(const Walker& w, const T* __restrict__ x, T
 // per kernel launch; chunk g of the launch lives in slot g % S, phase (g / S) & 1.
 __device__ __forceinline__ void ring_init(Shared& sh, const Params& P) {
   if (threadIdx.x == 0) {
+    // a slot is released by thread 0 (level-synchronous solves) or by every consumer
+    // warp (synchronisation-free solves)
+    const unsigned rel = P.tri_sf ? (unsigned)((blockDim.x >> 5) - 1) : 1u;
     for (int s = 0; s < P.ring_slots; ++s) {
       mbar_init(&sh.bar[s], 1);
-      mbar_init(&sh.ebar[s], 1);
+      mbar_init(&sh.ebar[s], rel);
     }
     sh.ring_seq = 0;
     sh.iflag[3] = 0;
@@ -93,11 +96,39 @@ __device__ __forceinline__ void ring_init(Shared& sh, const Params& P) {
   __syncthreads();
 }
 
-// One triangular solve in place on y (shared or global).  The last warp is the
-// producer: its lane 0 streams the factor's chunks into the ring with bulk copies,
-// refilling a slot once the consumers have released it.  The other warps solve: per
-// chunk they wait for it to land, solve its segments (levels) one after the other
-// with a barrier among the consumer warps between segments, and release the slot.
+// Producer of the chunk streams (lane 0 of the last warp): streams the factor's chunks
+// into the ring with bulk copies, refilling a slot once the consumers have released it
+// (the slot's "empty" barrier).  Returns the cycles spent waiting for free slots.
+__device__ __forceinline__ long long stream_chunks(const unsigned char* stream, const int2* tab, int nch,
+                                                   const Params& P, unsigned char* ring, int seq0, Shared& sh) {
+  const int S = P.ring_slots;
+  const int SB = P.slot_bytes;
+  long long twait = 0;
+  int2 pre[kMaxSlots];
+  for (int k = 0; k < S && k < nch; ++k) pre[k] = tab[k];
+  int slot = seq0 % S;
+  int g = seq0;
+  for (int c = 0; c < nch; ++c, ++g) {
+    unsigned char* dst = ring + (size_t)slot * SB;
+    if (g >= S) {  // the consumers must have released the slot's previous use
+      const long long tw = clock64();
+      if (!mbar_wait(&sh.ebar[slot], (unsigned)(((g / S) - 1) & 1))) sh.iflag[3] = 1;
+      twait += clock64() - tw;
+    }
+    // chunk c's descriptor: from the table for the first S chunks, else from the
+    // header of chunk c - S, still in this slot
+    const int2 tc = c < S ? pre[c] : ((const int2*)(dst + 16))[S - 1];
+    mbar_expect_tx(&sh.bar[slot], (unsigned)tc.y);
+    bulk_g2s(dst, stream + tc.x, (unsigned)tc.y, &sh.bar[slot]);
+    if (++slot == S) slot = 0;
+  }
+  return twait;
+}
+
+// One triangular solve in place on y (shared or global), level-synchronous.  The last
+// warp produces (stream_chunks); the other warps solve: per chunk they wait for it to
+// land, solve its segments (levels) one after the other with a barrier among the
+// consumer warps between segments, and release the slot.
 // Lower: y_r -= sum_t L_rt y_t.  Upper: y_r = (y_r - sum_t U_rt y_t) / U_rr.
 // Every wait gives up after ~1 s (status VMC_ERR_TIMEOUT).
 template <typename T>
@@ -113,26 +144,7 @@ __device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, boo
   const int nct = nt - 32;
   long long twait = 0;
   if (wid == nwarp - 1) {
-    if (lane == 0) {
-      int2 pre[kMaxSlots];
-      for (int k = 0; k < S && k < nch; ++k) pre[k] = tab[k];
-      int slot = seq0 % S;
-      int g = seq0;
-      for (int c = 0; c < nch; ++c, ++g) {
-        unsigned char* dst = ring + (size_t)slot * SB;
-        if (g >= S) {  // the consumers must have released the slot's previous use
-          const long long tw = clock64();
-          if (!mbar_wait(&sh.ebar[slot], (unsigned)(((g / S) - 1) & 1))) sh.iflag[3] = 1;
-          twait += clock64() - tw;
-        }
-        // chunk c's descriptor: from the table for the first S chunks, else from the
-        // header of chunk c - S, still in this slot
-        const int2 tc = c < S ? pre[c] : ((const int2*)(dst + 16))[S - 1];
-        mbar_expect_tx(&sh.bar[slot], (unsigned)tc.y);
-        bulk_g2s(dst, stream + tc.x, (unsigned)tc.y, &sh.bar[slot]);
-        if (++slot == S) slot = 0;
-      }
-    }
+    if (lane == 0) twait = stream_chunks(stream, tab, nch, P, ring, seq0, sh);
   } else {
     int slot = seq0 % S;
     unsigned parity = (unsigned)((seq0 / S) & 1);
@@ -193,17 +205,149 @@ __device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, boo
   __syncthreads();
 }
 
+// "Not yet solved" marker for the synchronisation-free solves: a quiet NaN with a
+// payload that arithmetic never produces (GPU arithmetic returns the canonical NaN).
+template <typename T>
+struct Pending;
+template <>
+struct Pending<float> {
+  static __device__ __forceinline__ float value() { return __int_as_float(0x7fc5a5a5); }
+  static __device__ __forceinline__ bool is(float v) { return __float_as_int(v) == 0x7fc5a5a5; }
+};
+template <>
+struct Pending<double> {
+  static __device__ __forceinline__ double value() { return __longlong_as_double(0x7ff8a5a5a5a5a5a5ll); }
+  static __device__ __forceinline__ bool is(double v) { return __double_as_longlong(v) == 0x7ff8a5a5a5a5a5a5ll; }
+};
+// Most retries of one row group's operands before giving up (status VMC_ERR_TIMEOUT).
+constexpr int kSpinMax = 1 << 22;
+
+// One triangular solve without level barriers: x = L^{-1} rhs (lower) or
+// x = U^{-1} rhs (upper), x in shared memory pre-filled with Pending.  Rows are taken
+// in the stream's level order, each by a group of G lanes (the level's group size),
+// a warp's groups holding consecutive rows of one level.  A warp waits only until the
+// operands of its own rows have been solved -- by whichever warp owns them -- instead
+// of for the whole previous level; it retries as a unit, so its lanes stay converged.
+// Rows only depend on earlier rows of the order, and every warp takes its rows in that
+// order, so the waits always end.  Each row's sum is taken in the same order as the
+// level-synchronous solve.
+template <typename T>
+__device__ __forceinline__ void tri_syncfree(const Walker& w, const Params& P, bool upper, const T* rhs, T* x,
+                                             Shared& sh) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nwarp = nt >> 5;
+  const unsigned char* stream = upper ? w.ustream : w.lstream;
+  const int2* tab = upper ? w.uchunk : w.lchunk;
+  const int nch = upper ? w.ctl->nchunk_u : w.ctl->nchunk_l;
+  const int S = P.ring_slots;
+  const int SB = P.slot_bytes;
+  unsigned char* ring = dyn_smem() + P.y_bytes;
+  const int seq0 = sh.ring_seq;
+  const int nct = nt - 32;
+  const volatile T* xv = x;
+  long long twait = 0;
+  if (wid == nwarp - 1) {
+    if (lane == 0) twait = stream_chunks(stream, tab, nch, P, ring, seq0, sh);
+  } else {
+    int slot = seq0 % S;
+    unsigned parity = (unsigned)((seq0 / S) & 1);
+    long long tdata = 0;
+    for (int c = 0; c < nch; ++c) {
+      const long long tw0 = clock64();
+      if (!mbar_wait(&sh.bar[slot], parity)) sh.iflag[3] = 1;
+      tdata += clock64() - tw0;
+      const unsigned char* ch = ring + (size_t)slot * SB;
+      const int4 hd = *(const int4*)ch;
+      const int nseg = hd.x, nr = hd.y, ne = hd.z;
+      const int4* seg = (const int4*)(ch + kChunkHdr);
+      const int* rws = (const int*)(ch + kChunkHdr + 16 * nseg);
+      const int* st = rws + pad4(nr);
+      const int* cl = st + pad4(nr + 1);
+      const T* vl = (const T*)(cl + pad4(ne));
+      const T* dv = (const T*)((const unsigned char*)vl + pad16((int)sizeof(T) * ne));
+      for (int sgi = 0; sgi < nseg; ++sgi) {
+        const int4 sm = seg[sgi];
+        const int r0 = sm.x, sr = sm.y, gs = sm.z;
+        const int G = 1 << gs;
+        const int gl = tid & (G - 1);
+        const int ng = nct >> gs;
+        for (int base = 0; base < sr; base += ng) {  // warp-uniform trip count
+          const int i = base + (tid >> gs);
+          const bool on = i < sr;
+          int r = 0, t0 = 0, e = 0;
+          if (on) {
+            r = rws[r0 + i];
+            t0 = st[r0 + i] + gl;
+            e = st[r0 + i + 1];
+          }
+          // sum and readiness in one pass; the warp retries together until every lane's
+          // operands were solved (so its lanes never diverge on a wait)
+          T part = 0;
+          for (int it = 0;; ++it) {
+            T p1 = 0, p2 = 0;
+            bool rdy = true;
+            int t = t0;
+            for (; t + G < e; t += 2 * G) {  // two entries in flight per lane
+              const T a = xv[cl[t]], b = xv[cl[t + G]];
+              rdy &= !Pending<T>::is(a) && !Pending<T>::is(b);
+              p1 += vl[t] * a;
+              p2 += vl[t + G] * b;
+            }
+            if (t < e) {
+              const T a = xv[cl[t]];
+              rdy &= !Pending<T>::is(a);
+              p1 += vl[t] * a;
+            }
+            if (__all_sync(0xffffffffu, rdy)) { part = p1 + p2; break; }
+            if (it >= kSpinMax || *(volatile int*)&sh.iflag[3]) { sh.iflag[3] = 1; break; }  // one give-up ends all waits
+          }
+          for (int o = G >> 1; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o, G);
+          if (on && gl == 0) {
+            T acc = rhs[r] - part;
+            if (upper) acc *= dv[r0 + i];
+            ((volatile T*)x)[r] = acc;
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.ebar[slot]);  // one arrival per consumer warp
+      if (++slot == S) { slot = 0; parity ^= 1u; }
+    }
+    if (tid == 0) w.ctl->cyc[PH_TRIDATA] += tdata;
+  }
+  if (wid == nwarp - 1 && lane == 0) w.ctl->cyc[PH_TRIWAIT] += twait;
+  __syncthreads();
+  if (tid == 0) sh.ring_seq = seq0 + nch;
+  __syncthreads();
+}
+
+// Both triangular solves on v (indexed by rows): returns the result L^{-1} then U^{-1}
+// applied, in factor-label order (shared or global memory).  Block-wide.
+template <typename T>
+__device__ __forceinline__ const T* tri_both(const Walker& w, const Params& P, const T* v, Shared& sh) {
+  const int n = w.n, tid = threadIdx.x, nt = blockDim.x;
+  T* y = P.y_smem ? (T*)dyn_smem() : (T*)w.tv;
+  if (P.tri_sf) {
+    T* x2 = (T*)(dyn_smem() + P.y_half);
+    for (int i = tid; i < n; i += nt) { y[i] = Pending<T>::value(); x2[i] = Pending<T>::value(); }
+    __syncthreads();
+    tri_syncfree<T>(w, P, false, v, y, sh);
+    tri_syncfree<T>(w, P, true, y, x2, sh);
+    return x2;
+  }
+  for (int i = tid; i < n; i += nt) y[i] = v[i];
+  __syncthreads();
+  tri_staged<T>(w, P, false, y, sh);
+  tri_staged<T>(w, P, true, y, sh);
+  return y;
+}
+
 // z = M v  (v indexed by rows, z by columns of A_p).  Block-wide, ends synchronised.
 template <typename T>
 __device__ __noinline__ void precond_apply(const Walker& w, const Params& P, const T* __restrict__ v,
                                            T* __restrict__ z, Shared& sh) {
   const int n = w.n, tid = threadIdx.x, nt = blockDim.x;
-  T* y = P.y_smem ? (T*)dyn_smem() : (T*)w.tv;
   const long long t0 = clock64();
-  for (int i = tid; i < n; i += nt) y[i] = v[i];
-  __syncthreads();
-  tri_staged<T>(w, P, false, y, sh);
-  tri_staged<T>(w, P, true, y, sh);
+  const T* y = tri_both<T>(w, P, v, sh);
   const long long t1 = clock64();
   if (tid == 0) {
     Ctl* c = w.ctl;

@@ -43,7 +43,8 @@ class vmc_solver_params(C.Structure):
                 ("gmres_m", C.c_int), ("max_restarts", C.c_int), ("inner_rtol", C.c_double),
                 ("ratio_tol", C.c_double), ("N_max", C.c_double), ("slow_factor", C.c_double),
                 ("max_updates", C.c_int), ("precision", C.c_int), ("engine", C.c_int),
-                ("block_threads", C.c_int), ("sm_refresh", C.c_int), ("refactor_lag", C.c_int)]
+                ("block_threads", C.c_int), ("sm_refresh", C.c_int), ("refactor_lag", C.c_int),
+                ("refactor_reorder", C.c_int), ("trisolve", C.c_int)]
 
 
 class vmc_stats(C.Structure):

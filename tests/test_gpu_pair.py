@@ -67,9 +67,12 @@ def _run(vmc, walkers=1, sweeps=2, calls=1, **kw):
         vmc.vmc_destroy(ctx)
 
 
+@pytest.mark.parametrize("reorder", [0, 1])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_pair_matches_oracle(vmc, reference, prec):
-    acc, rat, st = _run(vmc, precision=prec, max_updates=8, refactor_lag=4)
+def test_pair_matches_oracle(vmc, reference, prec, reorder):
+    """With and without re-pairing rows in the background (the chain is invariant under
+    a new row order, so either root is valid)."""
+    acc, rat, st = _run(vmc, precision=prec, max_updates=8, refactor_lag=4, refactor_reorder=reorder)
     _check(rat[0], acc[0], reference, 300)
     s = st[0]
     assert s["status"] == 0 and s["async_lag"] == 4

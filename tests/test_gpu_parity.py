@@ -142,13 +142,16 @@ def test_single_move_api_matches_oracle(vmc):
         vmc.vmc_destroy(ctx)
 
 
-@pytest.mark.parametrize("threads", [64, 128, 512])
+@pytest.mark.parametrize("trisolve", [0, 1])
+@pytest.mark.parametrize("threads", [64, 128, 256])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_block_sizes_match_oracle(vmc, threads, prec):
+def test_block_sizes_match_oracle(vmc, threads, prec, trisolve):
     """The CTA size changes the row-group split and reduction orders, not the ratios;
-    64 threads is one producer warp and a single consumer warp."""
+    64 threads is one producer warp and a single consumer warp.  Both triangular-solve
+    schedules (synchronisation-free, level-synchronous)."""
     wl = WL.PLAIN_216
-    ctx = vmc.vmc_create(wl.systems(), vmc.params(precision=0 if prec == "fp64" else 1, block_threads=threads))
+    ctx = vmc.vmc_create(wl.systems(), vmc.params(precision=0 if prec == "fp64" else 1, block_threads=threads,
+                                                  trisolve=trisolve))
     try:
         vmc.vmc_init_positions(ctx, wl.seeds(), wl.jitter)
         acc, rat = vmc.vmc_sweep(ctx, 2, wl.sigma, wl.seeds())
