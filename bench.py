@@ -47,6 +47,36 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def sources_digest() -> str:
+    """SHA-256 over the CUDA sources and the C header (identifies the kernels' build)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1008_5113_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)) + ["../../include/vmc.h"]:
+        path = os.path.normpath(os.path.join(csrc, f))
+        if os.path.isfile(path):
+            h.update(f.encode())
+            h.update(open(path, "rb").read())
+    return h.hexdigest()
+
+
+def profiled_traffic(summary: str):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu summary, or None
+    when the summary is absent or was taken from other kernel sources."""
+    path = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "sources_sha256")):
+            k, v = line.strip().strip("`").split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("sources_sha256") != sources_digest() or "traffic_bytes_per_launch" not in fields:
+        return None
+    return float(fields["traffic_bytes_per_launch"])
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -163,6 +193,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-kernels", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -208,10 +239,13 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     seeds_dev = torch.tensor(seeds, dtype=torch.int64, device="cuda")
 
-    def timed_sweeps(ctx, steps, warmup):
+    def timed_sweeps(ctx, steps, warmup, keep_state=None):
         for _ in range(warmup):
             vmc.vmc_sweep_async(ctx, 1, SIGMA, seeds_dev)
         vmc.vmc_synchronize(ctx)
+        if keep_state is not None:  # walker 0 where the timed sweeps start (for the plain path)
+            keep_state["R0"] = vmc.vmc_get_positions(ctx, 0)
+            keep_state["sweep"] = vmc.vmc_sweep_count(ctx)
         vmc.vmc_reset_stats(ctx)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         if world > 1:
@@ -232,16 +266,23 @@ def main():
     # ---- headline: batched FP64, persistent engine (one launch per sweep) ------------
     ctx = make(vmc.PREC_FP64, vmc.ENGINE_PERSISTENT)
     refactoring = refactor_mode(ctx)
+    state = {}
     kernel_name = "k_sweep_pair" if vmc.vmc_get_stats(ctx, 0)["async_lag"] > 0 else "k_sweep"
     with Clocks(dev) as clk:
-        total_ms, per_ms, wall = timed_sweeps(ctx, args.steps, args.warmup)
+        total_ms, per_ms, wall = timed_sweeps(ctx, args.steps, args.warmup, keep_state=state)
     stats = [vmc.vmc_get_stats(ctx, w) for w in range(WALKERS)]
     ratios_local = sum(s["proposals"] for s in stats)
     assert ratios_local == args.steps * WALKERS * N, (ratios_local, args.steps)
     ratios_all, t_max = replicas.reduce_run(ratios_local, total_ms)
     value = replicas.throughput(ratios_all, t_max / 1000.0)
     alg_bytes = sum(s["alg_bytes"] for s in stats)
-    # ---- e2e: public host API, host seeds in, host logs out, every step -------------------
+    vmc.vmc_destroy(ctx)
+    # ---- e2e: public host API, host seeds in, host logs out, every step; a fresh context
+    #      brought to the same state, so the timed sweeps are the same sweeps as above -----
+    ctx = make(vmc.PREC_FP64, vmc.ENGINE_PERSISTENT)
+    for _ in range(args.warmup):
+        vmc.vmc_sweep_async(ctx, 1, SIGMA, seeds_dev)
+    vmc.vmc_synchronize(ctx)
     host_seeds = np.array(seeds, dtype=np.uint64)
     acc_log = np.zeros(WALKERS * N, dtype=np.uint8)
     rat_log = np.zeros(WALKERS * N)
@@ -261,16 +302,18 @@ def main():
     if rank == 0:
         # ---- mixed precision, same workload ----------------------------------------------
         ctxm = make(vmc.PREC_MIXED, vmc.ENGINE_PERSISTENT)
-        tm, _, _ = timed_sweeps(ctxm, max(2, args.steps // 2), 3)
+        tm, _, _ = timed_sweeps(ctxm, args.steps, args.warmup)
         sm = [vmc.vmc_get_stats(ctxm, w) for w in range(WALKERS)]
         extra["mixed_value"] = sum(s["proposals"] for s in sm) / (tm / 1000.0)
         vmc.vmc_destroy(ctxm)
         # ---- plain FP64 one-walker-per-launch path (bounded sample: 1 walker, 1 sweep) ---
+        # started from walker 0's configuration at the first timed sweep, with that sweep's
+        # random numbers, so that both paths solve equally conditioned matrices
         if not args.no_plain:
             ctxp = make(vmc.PREC_FP64, vmc.ENGINE_PLAIN, nw=1)
+            vmc.vmc_set_positions(ctxp, 0, state["R0"])
+            vmc.vmc_set_sweep_count(ctxp, state["sweep"])
             sd1 = seeds_dev[:1]
-            vmc.vmc_sweep_async(ctxp, 1, SIGMA, sd1)
-            vmc.vmc_synchronize(ctxp)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -281,8 +324,38 @@ def main():
             plain = N / (e0.elapsed_time(e1) / 1000.0)
             vmc.vmc_destroy(ctxp)
             extra["plain_fp64_value"] = plain
+            extra["plain_fp64_sample"] = (f"walker 0 from its configuration at sweep {state['sweep']}, "
+                                          f"one sweep ({N} launches)")
             extra["speedup_vs_plain"] = value / plain
             extra["speedup_vs_plain_mixed"] = extra["mixed_value"] / plain
+    if rank == 0 and not args.no_kernels:
+        # ---- per-kernel rooflines at the HBM-sized configurations (CTA per walker, 152
+        #      walkers = one per SM): triangular solves and SpMV, FP32 (mixed mode) -----
+        hbm_peak, _ = peaks()
+        kr = {}
+        for K in (16, 32):
+            ctxk = vmc.vmc_create([(K, 0, A, KAPPA, RC)] * 152, vmc.params(precision=vmc.PREC_MIXED), stream=stream)
+            vmc.vmc_init_positions(ctxk, list(range(1, 153)), JITTER)
+            reps = 40 if K == 16 else 10
+            for which, name in ((0, "trisolve"), (1, "spmv")):
+                vmc.vmc_kernel_bench(ctxk, which, 2)
+                vmc.vmc_synchronize(ctxk)
+                vmc.vmc_reset_stats(ctxk)
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                vmc.vmc_kernel_bench(ctxk, which, reps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                vmc.vmc_synchronize(ctxk)
+                ms = e0.elapsed_time(e1)
+                by = sum(vmc.vmc_get_stats(ctxk, w)["alg_bytes"] for w in range(152))
+                gbs = by / (ms / 1000.0) / 1e9
+                kr[f"{name}_sc{K}_n{K ** 3}_w152_f32"] = {
+                    "us_per_apply": 1000.0 * ms / reps, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": gbs / hbm_peak, "bytes_per_apply": by / reps}
+            vmc.vmc_destroy(ctxk)
+        extra["kernel_rooflines"] = kr
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -305,7 +378,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * WALKERS,
                 "d2h_bytes_per_step": 9 * WALKERS * N},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm, "traffic": profiled_traffic(f"{kernel_name}_sc10_n1000_w64_fp64.md"),
                      "note": f"{kernel_name}, algorithmic bytes from the kernel's per-phase counter; peak "
                              f"{peak_kind}"},
         "solver": {"inner_its_per_ratio": its,

@@ -41,21 +41,40 @@ template <> struct Vec4<double> {
 };
 
 // Dot product of Slater slot p (len entries) with x: 16-byte loads of four column
-// indices and four values at a time; entries past len are masked (slots hold valid
-// column indices there, so the gathers stay in bounds).
+// indices and four values at a time (slot capacities are multiples of 4); entries
+// past len are neither gathered nor summed.
 template <typename T, typename X>
 __device__ __forceinline__ X slot_dot(const int* __restrict__ cols, const T* __restrict__ vals, int len,
                                       const X* __restrict__ x) {
+  // up to 16 entries at a time: their index and value loads are all issued, then their
+  // gathers, then the products are summed in entry order
+  constexpr int U = 4;
   X acc = 0;
-  for (int q = 0; q < len; q += 4) {
-    const int4 c = *reinterpret_cast<const int4*>(cols + q);
-    Vec4<T> v;
-    v.load(vals + q);
-    const X x0 = x[c.x], x1 = x[c.y], x2 = x[c.z], x3 = x[c.w];
-    acc += (X)v.v[0] * x0;
-    if (q + 1 < len) acc += (X)v.v[1] * x1;
-    if (q + 2 < len) acc += (X)v.v[2] * x2;
-    if (q + 3 < len) acc += (X)v.v[3] * x3;
+  for (int q0 = 0; q0 < len; q0 += 4 * U) {
+    int4 c[U];
+    Vec4<T> v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c[u] = make_int4(0, 0, 0, 0);
+      if (q0 + 4 * u < len) {
+        c[u] = *reinterpret_cast<const int4*>(cols + q0 + 4 * u);
+        v[u].load(vals + q0 + 4 * u);
+      }
+    }
+    X xv[4 * U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = q0 + 4 * u;
+      xv[4 * u + 0] = q + 0 < len ? x[c[u].x] : (X)0;
+      xv[4 * u + 1] = q + 1 < len ? x[c[u].y] : (X)0;
+      xv[4 * u + 2] = q + 2 < len ? x[c[u].z] : (X)0;
+      xv[4 * u + 3] = q + 3 < len ? x[c[u].w] : (X)0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (q0 + 4 * u + k < len) acc += (X)v[u].v[k] * xv[4 * u + k];
   }
   return acc;
 }
