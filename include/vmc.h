@@ -109,6 +109,10 @@ typedef struct {
                           next level's rows gathered ahead of it); 1 = synchronisation-free
                           when both solve vectors fit in shared memory (a warp waits only for
                           the entries its rows read), else level-synchronous (0) */
+  int graphs;          /* STEP and PLAIN engines: capture one sweep's launches as a CUDA graph
+                          (with the sweep index kept on the device) and replay it once per
+                          sweep (1), or launch them one by one (0).  Used when the call makes
+                          one sweep or keeps no logs (1) */
 } vmc_solver_params;
 
 /* Per-walker statistics (Sec. 4 Tables 2 and 3 analogues). */
@@ -151,6 +155,33 @@ typedef struct {
 
 /* Fill p with the defaults above. */
 vmc_status vmc_default_params(vmc_solver_params* p);
+
+/* One autotuner trial (see vmc_autotune). */
+typedef struct {
+  int engine;          /* VMC_ENGINE_PERSISTENT or VMC_ENGINE_STEP                        */
+  int block_threads;   /* threads per walker CTA                                          */
+  int max_updates;     /* update-chain length before a refactorisation                    */
+  int refactor_lag;    /* the lag in effect: > 0 background refactorisation (walker pairs) */
+  double ratios_per_s; /* measured determinant ratios per second (0 when the trial failed) */
+  int status;          /* vmc_status of the trial                                        */
+} vmc_tune_trial;
+
+/* Autotuner: picks the launch mapping for these walkers by timing short trials on the
+ * device.  Candidates: a CTA pair per walker with background refactorisation (when the
+ * pairs fit), a CTA per walker (persistent), one launch per step (STEP engine); 128 or
+ * 256 threads per CTA; then max_updates of 32, 64 or 128 for the best of those.  Each
+ * trial creates a context from `params` with the candidate's fields, starts the walkers
+ * from `seeds` and `jitter`, runs one untimed and one timed partial sweep of `steps`
+ * moves per walker (proposal width sigma) and destroys the context.  The mapping does
+ * not change the method -- only how it is laid out on the GPU, and the rounding.
+ * params (in/out): the base parameters; on return engine, block_threads, max_updates and
+ * refactor_lag hold the fastest trial's.  trials (nullable): receives up to max_trials
+ * trial records, *n_trials (nullable) their number.  stream as in vmc_create.  Returns
+ * VMC_ERR_INVALID on bad arguments or a DENSE_SM engine, the first failure if every trial
+ * fails, else VMC_OK. */
+vmc_status vmc_autotune(const vmc_system* systems, int n_walkers, vmc_solver_params* params, const uint64_t* seeds,
+                        double jitter, double sigma, int steps, vmc_tune_trial* trials, int max_trials,
+                        int* n_trials, void* stream);
 
 /* Create a context for n_walkers walkers; systems[w] is walker w's system
  * (walkers may differ in size: an uneven batch).  stream: a cudaStream_t (or NULL

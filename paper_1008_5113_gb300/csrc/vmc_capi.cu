@@ -148,6 +148,15 @@ struct vmc_ctx {
   Walker* dWf = nullptr;
   Ctl* dShadow = nullptr;
   int launch_seq = 0;
+  // CUDA graph of one sweep of the STEP / PLAIN engines (replayed once per sweep)
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  long long* d_sweep = nullptr;
+  const void* g_seeds = nullptr;
+  const void* g_acc = nullptr;
+  const void* g_ratio = nullptr;
+  double g_sigma = 0.0;
+  int g_limit = -1;
 };
 
 static vmc_status fail(vmc_ctx* c, vmc_status s, const std::string& msg) {
@@ -185,6 +194,7 @@ extern "C" vmc_status vmc_default_params(vmc_solver_params* p) {
   p->refactor_lag = -1;
   p->refactor_reorder = 0;
   p->trisolve = 0;
+  p->graphs = 1;
   return VMC_OK;
 }
 
@@ -646,6 +656,9 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
 
 extern "C" vmc_status vmc_destroy(vmc_ctx* ctx) {
   if (!ctx) return VMC_ERR_INVALID;
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  if (ctx->d_sweep) cudaFree(ctx->d_sweep);
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->d_seeds) cudaFree(ctx->d_seeds);
   if (ctx->d_acc) cudaFree(ctx->d_acc);
@@ -756,6 +769,68 @@ static vmc_status ensure_logs(vmc_ctx* ctx, size_t entries) {
   return VMC_OK;
 }
 
+// The launches of one sweep of the STEP or PLAIN engine (sweep index read from
+// ctx->d_sweep when sweep_dev is set).
+static cudaError_t step_launches(vmc_ctx* ctx, int n_sweeps, int s_local, long long s0, double sigma,
+                                 const uint64_t* d_seeds, uint8_t* acc, double* ratio, const long long* sweep_dev,
+                                 cudaStream_t stream) {
+  LaunchCfg L = cfg(ctx);
+  L.stream = stream;
+  const int lim = ctx->P.step_limit;
+  if (ctx->prm.engine == VMC_ENGINE_STEP) {
+    const int qn = lim > 0 ? std::min(ctx->max_n, lim) : ctx->max_n;
+    for (int q = 0; q < qn; ++q) {
+      const cudaError_t e = launch_step(L, ctx->dW, 0, ctx->nw, ctx->P, q, n_sweeps, s_local, s0, sigma, d_seeds, acc,
+                                        ratio, sweep_dev);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  for (int w = 0; w < ctx->nw; ++w) {  // PLAIN: one walker per launch
+    const int qn = lim > 0 ? std::min(ctx->hw[w].n, lim) : ctx->hw[w].n;
+    for (int q = 0; q < qn; ++q) {
+      const cudaError_t e = launch_step(L, ctx->dW, w, 1, ctx->P, q, n_sweeps, s_local, s0, sigma, d_seeds, acc, ratio,
+                                        sweep_dev);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+// Capture (or reuse) the graph of one sweep: the step launches, then the advance of the
+// device-side sweep index.  Captured on a private stream (the legacy default stream
+// cannot be captured) and replayed on the context's stream.
+static vmc_status sweep_graph(vmc_ctx* ctx, double sigma, const uint64_t* d_seeds, uint8_t* acc, double* ratio) {
+  if (ctx->graph && ctx->g_seeds == d_seeds && ctx->g_acc == acc && ctx->g_ratio == ratio && ctx->g_sigma == sigma &&
+      ctx->g_limit == ctx->P.step_limit)
+    return VMC_OK;
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  if (!ctx->d_sweep) CK(cudaMalloc((void**)&ctx->d_sweep, sizeof(long long)), "sweep index");
+  if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking), "capture stream");
+  CK(prepare_step_kernels(cfg(ctx)), "step kernel attributes");
+  CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal), "begin graph capture");
+  cudaError_t e = step_launches(ctx, 1, 0, 0, sigma, d_seeds, acc, ratio, ctx->d_sweep, ctx->capture_stream);
+  if (e == cudaSuccess) e = launch_next_sweep(ctx->d_sweep, ctx->capture_stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    ctx->graph = nullptr;
+    return cuda_fail(ctx, e, "sweep graph");
+  }
+  ctx->g_seeds = d_seeds;
+  ctx->g_acc = acc;
+  ctx->g_ratio = ratio;
+  ctx->g_sigma = sigma;
+  ctx->g_limit = ctx->P.step_limit;
+  return VMC_OK;
+}
+
 static vmc_status enqueue_sweeps(vmc_ctx* ctx, int n_sweeps, double sigma, const uint64_t* d_seeds, uint8_t* acc,
                                  double* ratio) {
   const LaunchCfg L = cfg(ctx);
@@ -770,15 +845,15 @@ static vmc_status enqueue_sweeps(vmc_ctx* ctx, int n_sweeps, double sigma, const
        "sweep kernel (walker pairs)");
   } else if (eng == VMC_ENGINE_PERSISTENT) {
     CK(launch_sweep(L, ctx->dW, 0, ctx->nw, ctx->P, n_sweeps, s0, sigma, d_seeds, acc, ratio), "sweep kernel");
-  } else if (eng == VMC_ENGINE_STEP) {
+  } else if (ctx->prm.graphs && (n_sweeps == 1 || (!acc && !ratio))) {
+    // STEP / PLAIN: replay a captured graph of one sweep's launches per sweep
+    vmc_status st = sweep_graph(ctx, sigma, d_seeds, acc, ratio);
+    if (st != VMC_OK) return st;
+    CK(launch_set_sweep(ctx->d_sweep, s0, ctx->stream), "sweep index");
+    for (int s = 0; s < n_sweeps; ++s) CK(cudaGraphLaunch(ctx->graph, ctx->stream), "sweep graph");
+  } else {  // STEP / PLAIN, launch by launch
     for (int s = 0; s < n_sweeps; ++s)
-      for (int q = 0; q < ctx->max_n; ++q)
-        CK(launch_step(L, ctx->dW, 0, ctx->nw, ctx->P, q, n_sweeps, s, s0, sigma, d_seeds, acc, ratio), "step kernel");
-  } else {  // PLAIN: one walker per launch, one launch per move step
-    for (int s = 0; s < n_sweeps; ++s)
-      for (int w = 0; w < ctx->nw; ++w)
-        for (int q = 0; q < ctx->hw[w].n; ++q)
-          CK(launch_step(L, ctx->dW, w, 1, ctx->P, q, n_sweeps, s, s0, sigma, d_seeds, acc, ratio), "step kernel");
+      CK(step_launches(ctx, n_sweeps, s, s0, sigma, d_seeds, acc, ratio, nullptr, ctx->stream), "step kernel");
   }
   ctx->sweeps += n_sweeps;
   return VMC_OK;
@@ -1018,4 +1093,95 @@ extern "C" vmc_status vmc_philox_device(const uint32_t* ctr, const uint32_t* key
   if (dk) cudaFree(dk);
   if (dout) cudaFree(dout);
   return st;
+}
+
+// ---- autotuner ---------------------------------------------------------------------
+static vmc_status tune_trial(const vmc_system* systems, int nw, const vmc_solver_params& p, const uint64_t* seeds,
+                             double jitter, double sigma, int steps, void* stream, double* rate, int* lag) {
+  vmc_ctx* c = nullptr;
+  *rate = 0.0;
+  *lag = 0;
+  vmc_status st = vmc_create(systems, nw, &p, stream, &c);
+  if (st == VMC_OK) st = vmc_init_positions(c, seeds, jitter);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (st == VMC_OK) {
+    *lag = c->P.af_lag;
+    c->P.step_limit = steps;
+    long long moves = 0;
+    for (int w = 0; w < nw; ++w) moves += std::min(c->hw[w].n, steps);
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = VMC_ERR_CUDA;
+    if (st == VMC_OK) st = enqueue_sweeps(c, 1, sigma, c->d_seeds, nullptr, nullptr);  // untimed
+    if (st == VMC_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = VMC_ERR_CUDA;
+    if (st == VMC_OK) st = enqueue_sweeps(c, 1, sigma, c->d_seeds, nullptr, nullptr);  // timed
+    if (st == VMC_OK && cudaEventRecord(e1, c->stream) != cudaSuccess) st = VMC_ERR_CUDA;
+    if (st == VMC_OK) st = check_walker_status(c);
+    float ms = 0.0f;
+    if (st == VMC_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.0f) *rate = moves / (ms * 1e-3);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (c) vmc_destroy(c);
+  return st;
+}
+
+extern "C" vmc_status vmc_autotune(const vmc_system* systems, int n_walkers, vmc_solver_params* params,
+                                   const uint64_t* seeds, double jitter, double sigma, int steps,
+                                   vmc_tune_trial* trials, int max_trials, int* n_trials, void* stream) {
+  if (n_trials) *n_trials = 0;
+  if (!systems || !params || !seeds || n_walkers <= 0 || steps <= 0 || !(sigma >= 0.0) || !(jitter >= 0.0) ||
+      (trials && max_trials < 0) || params->engine == VMC_ENGINE_DENSE_SM)
+    return VMC_ERR_INVALID;
+  struct Cand { int engine, threads, mu, lag; };
+  std::vector<vmc_tune_trial> done;
+  vmc_status first_err = VMC_OK;
+  auto run = [&](const Cand& cd) -> double {
+    vmc_solver_params p = *params;
+    p.engine = cd.engine;
+    p.block_threads = cd.threads;
+    p.max_updates = cd.mu;
+    p.refactor_lag = cd.lag;
+    double rate = 0.0;
+    int lag = 0;
+    const vmc_status st = tune_trial(systems, n_walkers, p, seeds, jitter, sigma, steps, stream, &rate, &lag);
+    if (st != VMC_OK && first_err == VMC_OK) first_err = st;
+    vmc_tune_trial t{cd.engine, cd.threads, cd.mu, lag, st == VMC_OK ? rate : 0.0, (int)st};
+    done.push_back(t);
+    return st == VMC_OK ? rate : 0.0;
+  };
+  // phase 1: mapping x CTA size at the given chain length
+  const int mu0 = params->max_updates;
+  double best = -1.0;
+  Cand bc{VMC_ENGINE_PERSISTENT, 256, mu0, 0};
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const bool pairs_fit = 2 * n_walkers <= nsm && mu0 >= 2;  // the rule of refactor_lag = -1
+  for (int threads : {128, 256}) {
+    const Cand cands[3] = {{VMC_ENGINE_PERSISTENT, threads, mu0, -1},
+                           {VMC_ENGINE_PERSISTENT, threads, mu0, 0},
+                           {VMC_ENGINE_STEP, threads, mu0, 0}};
+    for (const Cand& cd : cands) {
+      if (cd.lag == -1 && !pairs_fit) continue;  // would be the same as the next candidate
+      const double r = run(cd);
+      if (r > best) { best = r; bc = cd; bc.lag = done.back().refactor_lag; }
+    }
+  }
+  // phase 2: chain length for the best mapping
+  for (int mu : {32, 64, 128}) {
+    if (mu == mu0 || mu > kMaxUpd) continue;
+    Cand cd = bc;
+    cd.mu = mu;
+    if (bc.lag > 0) cd.lag = -1;  // background lag follows the chain length (mu / 2)
+    const double r = run(cd);
+    if (r > best) { best = r; bc = cd; bc.lag = done.back().refactor_lag; }
+  }
+  if (trials)
+    for (int i = 0; i < (int)done.size() && i < max_trials; ++i) trials[i] = done[i];
+  if (n_trials) *n_trials = (int)done.size();
+  if (best <= 0.0) return first_err != VMC_OK ? first_err : VMC_ERR_INVALID;
+  params->engine = bc.engine;
+  params->block_threads = bc.threads;
+  params->max_updates = bc.mu;
+  params->refactor_lag = bc.lag;
+  return VMC_OK;
 }

@@ -146,6 +146,7 @@ struct Params {
   int ilu64;        // 1: the ILUTP working row is FP64 whatever the stored precision
   int af_lag;       // background refactorisation: accepts between a snapshot and its use (0: off)
   int af_reorder;   // 1: background refactorisations re-pair particles and orbitals first
+  int step_limit;   // > 0: a sweep moves only particles 0 .. step_limit - 1 (autotuner trials)
   int tri_sf;       // 1: synchronisation-free triangular solves (two solve vectors in shared memory)
   int y_half;       // byte offset of the second solve vector (tri_sf)
 };

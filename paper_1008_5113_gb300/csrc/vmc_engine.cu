@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_sweep(const Walker* __restri
   const uint64_t seed = seeds[wi];
   const int n = w.n;
   for (int s = 0; s < n_sweeps; ++s)
-    for (int k = 0; k < n; ++k) {
+    for (int k = 0; k < (P.step_limit > 0 ? min(n, P.step_limit) : n); ++k) {
       const long long idx = (long long)n_sweeps * w.log_base + (long long)s * n + k;
       mc_step<T>(w, P, k, seed, (uint32_t)(sweep0 + s), sigma, acc_log ? acc_log + idx : nullptr,
                  ratio_log ? ratio_log + idx : nullptr, sh);
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_sweep_pair(const Walker* __r
   const uint64_t seed = seeds[wi];
   const int n = w0.n;
   for (int s = 0; s < n_sweeps; ++s)
-    for (int k = 0; k < n; ++k) {
+    for (int k = 0; k < (P.step_limit > 0 ? min(n, P.step_limit) : n); ++k) {
       af_step_begin<T>(w0, P, sh);
       const Walker& w = active_of(w0);
       const long long idx = (long long)n_sweeps * w.log_base + (long long)s * n + k;
@@ -434,12 +434,14 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_sweep_pair(const Walker* __r
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads, 2) k_step(const Walker* __restrict__ W, int walker0, Params P, int q, int n_sweeps,
                                                int s_local, long long sweep0, double sigma,
-                                               const uint64_t* __restrict__ seeds, uint8_t* acc_log, double* ratio_log) {
+                                               const uint64_t* __restrict__ seeds, uint8_t* acc_log, double* ratio_log,
+                                               const long long* __restrict__ sweep_dev) {
   __shared__ Shared sh;
   const int wi = walker0 + blockIdx.x;
   const Walker& w = active_of(W[wi]);
   if (q >= w.n) return;
   ring_init(sh, P);
+  if (sweep_dev) sweep0 = *sweep_dev;  // graph replays: the sweep index lives on the device
   const long long idx = (long long)n_sweeps * w.log_base + (long long)s_local * w.n + q;
   mc_step<T>(w, P, q, seeds[wi], (uint32_t)(sweep0 + s_local), sigma, acc_log ? acc_log + idx : nullptr,
              ratio_log ? ratio_log + idx : nullptr, sh);
@@ -674,11 +676,26 @@ cudaError_t launch_sweep_pair(const LaunchCfg& L, const Walker* W, int walker0, 
   return cudaLaunchKernelEx(&lc, k_sweep_pair<float>, W, walker0, P, n_sweeps, sweep0, sigma, seeds, acc, ratio,
                             launch_id);
 }
+// Advance / set the device-side sweep index of the replayed sweep graphs.
+__global__ void k_next_sweep(long long* sweep_dev) { *sweep_dev += 1; }
+__global__ void k_set_sweep(long long* sweep_dev, long long v) { *sweep_dev = v; }
+cudaError_t launch_set_sweep(long long* sweep_dev, long long v, cudaStream_t s) {
+  k_set_sweep<<<1, 1, 0, s>>>(sweep_dev, v);
+  return cudaGetLastError();
+}
+cudaError_t launch_next_sweep(long long* sweep_dev, cudaStream_t s) {
+  k_next_sweep<<<1, 1, 0, s>>>(sweep_dev);
+  return cudaGetLastError();
+}
+cudaError_t prepare_step_kernels(const LaunchCfg& L) {
+  return L.fp64 ? prep(k_step<double>, L) : prep(k_step<float>, L);
+}
 cudaError_t launch_step(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int q,
                         int n_sweeps, int s_local, long long sweep0, double sigma, const uint64_t* seeds,
-                        uint8_t* acc, double* ratio) {
-  if (L.fp64) VMC_LAUNCH(k_step<double>, nwalk, W, walker0, P, q, n_sweeps, s_local, sweep0, sigma, seeds, acc, ratio);
-  VMC_LAUNCH(k_step<float>, nwalk, W, walker0, P, q, n_sweeps, s_local, sweep0, sigma, seeds, acc, ratio);
+                        uint8_t* acc, double* ratio, const long long* sweep_dev) {
+  if (L.fp64) VMC_LAUNCH(k_step<double>, nwalk, W, walker0, P, q, n_sweeps, s_local, sweep0, sigma, seeds, acc, ratio,
+                         sweep_dev);
+  VMC_LAUNCH(k_step<float>, nwalk, W, walker0, P, q, n_sweeps, s_local, sweep0, sigma, seeds, acc, ratio, sweep_dev);
 }
 cudaError_t launch_ratio(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int k, const double r[3]) {
   if (L.fp64) VMC_LAUNCH(k_ratio<double>, 1, W, wi, P, k, r[0], r[1], r[2]);

@@ -25,9 +25,15 @@ cudaError_t launch_sweep(const LaunchCfg& L, const Walker* W, int walker0, int n
 cudaError_t launch_sweep_pair(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P,
                               int n_sweeps, long long sweep0, double sigma, const uint64_t* seeds, uint8_t* acc,
                               double* ratio, int launch_id);
+// sweep_dev: nullptr, or a device scalar holding the sweep index (graph replays; then
+// sweep0 is ignored)
 cudaError_t launch_step(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int q,
                         int n_sweeps, int s_local, long long sweep0, double sigma, const uint64_t* seeds,
-                        uint8_t* acc, double* ratio);
+                        uint8_t* acc, double* ratio, const long long* sweep_dev = nullptr);
+cudaError_t launch_next_sweep(long long* sweep_dev, cudaStream_t s);
+cudaError_t launch_set_sweep(long long* sweep_dev, long long v, cudaStream_t s);
+// Sets the step kernels' shared-memory attribute (before a graph capture).
+cudaError_t prepare_step_kernels(const LaunchCfg& L);
 cudaError_t launch_ratio(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int k, const double r[3]);
 cudaError_t launch_accept(const LaunchCfg& L, const Walker* W, int wi, const Params& P);
 cudaError_t launch_init_positions(const LaunchCfg& L, const Walker* W, int nwalk, const uint64_t* seeds, double jitter);

@@ -44,7 +44,8 @@ class vmc_solver_params(C.Structure):
                 ("ratio_tol", C.c_double), ("N_max", C.c_double), ("slow_factor", C.c_double),
                 ("max_updates", C.c_int), ("precision", C.c_int), ("engine", C.c_int),
                 ("block_threads", C.c_int), ("sm_refresh", C.c_int), ("refactor_lag", C.c_int),
-                ("refactor_reorder", C.c_int), ("trisolve", C.c_int)]
+                ("refactor_reorder", C.c_int), ("trisolve", C.c_int),
+                ("graphs", C.c_int)]
 
 
 class vmc_stats(C.Structure):
@@ -60,6 +61,11 @@ class vmc_stats(C.Structure):
                 ("chunks_L", C.c_int), ("chunks_U", C.c_int), ("refactors_async", C.c_int64),
                 ("async_wait_cycles", C.c_int64), ("async_factor_cycles", C.c_int64), ("factor_set", C.c_int),
                 ("async_lag", C.c_int)]
+
+
+class vmc_tune_trial(C.Structure):
+    _fields_ = [("engine", C.c_int), ("block_threads", C.c_int), ("max_updates", C.c_int),
+                ("refactor_lag", C.c_int), ("ratios_per_s", C.c_double), ("status", C.c_int)]
 
 
 # name -> (restype, argtypes); every symbol the header declares
@@ -92,6 +98,8 @@ _SIG = {
                                     C.c_void_p]),
     "vmc_noalloc_capacity": (C.c_size_t, []),
     "vmc_noalloc_last_error": (C.c_char_p, []),
+    "vmc_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int,
+                               C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -308,3 +316,16 @@ def params(**kw) -> vmc_solver_params:
             raise AttributeError(k)
         setattr(p, k, v)
     return p
+
+
+def vmc_autotune(systems, params: vmc_solver_params, seeds, jitter: float, sigma: float, steps: int, stream=None):
+    """Returns (the tuned parameters, the list of trials as dicts)."""
+    arr = (vmc_system * len(systems))(*[vmc_system(int(K), int(lat), float(a), float(k), float(rc))
+                                        for (K, lat, a, k, rc) in systems])
+    p = vmc_solver_params.from_buffer_copy(params)
+    s = np.ascontiguousarray(seeds, dtype=np.uint64)
+    trials = (vmc_tune_trial * 16)()
+    nt = C.c_int(0)
+    _check(lib().vmc_autotune(arr, len(systems), C.byref(p), _p(s), float(jitter), float(sigma), int(steps), trials, 16,
+                              C.byref(nt), _stream_handle(stream)))
+    return p, [{name: getattr(trials[i], name) for name, _ in vmc_tune_trial._fields_} for i in range(nt.value)]

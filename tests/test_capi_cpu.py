@@ -82,7 +82,7 @@ def test_struct_layouts_match_the_header(vmc, tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("gcc not available")
     structs = {"vmc_system": vmc.vmc_system, "vmc_solver_params": vmc.vmc_solver_params,
-               "vmc_stats": vmc.vmc_stats}
+               "vmc_stats": vmc.vmc_stats, "vmc_tune_trial": vmc.vmc_tune_trial}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "vmc.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
@@ -99,3 +99,16 @@ def test_struct_layouts_match_the_header(vmc, tmp_path):
         assert int(out[name]) == C.sizeof(cls), name
         for field, _ in cls._fields_:
             assert int(out[f"{name}.{field}"]) == getattr(cls, field).offset, f"{name}.{field}"
+
+
+def test_autotune_rejects_bad_arguments_without_a_gpu(vmc):
+    lib = vmc.lib()
+    p = vmc.vmc_default_params()
+    sysarr = (vmc.vmc_system * 1)(vmc.vmc_system(6, 0, 1.0, 2.0, 1.5))
+    seeds = (C.c_uint64 * 1)(1)
+    n = C.c_int(-1)
+    assert lib.vmc_autotune(None, 1, C.byref(p), seeds, 0.1, 0.2, 64, None, 0, C.byref(n), None) == 1
+    assert n.value == 0
+    assert lib.vmc_autotune(sysarr, 1, C.byref(p), seeds, 0.1, 0.2, 0, None, 0, None, None) == 1
+    p.engine = vmc.ENGINE_DENSE_SM
+    assert lib.vmc_autotune(sysarr, 1, C.byref(p), seeds, 0.1, 0.2, 64, None, 0, None, None) == 1
