@@ -40,23 +40,24 @@ template <> struct Vec4<double> {
   }
 };
 
-// Dot product of Slater slot p (len entries) with x: 16-byte loads of four column
-// indices and four values at a time (slot capacities are multiples of 4); entries
-// past len are neither gathered nor summed.
+// Dot product of Slater slot p (len entries, capacity cap) with x: 16-byte loads of
+// four column indices and four values at a time (cap is a multiple of 4).  Up to 16
+// entries at a time have their index and value loads issued together -- bounded by the
+// slot's capacity, not its length, so the first ones need not wait for len -- then
+// their gathers (entries < len only), then the products are summed in entry order.
 template <typename T, typename X>
-__device__ __forceinline__ X slot_dot(const int* __restrict__ cols, const T* __restrict__ vals, int len,
+__device__ __forceinline__ X slot_dot(const int* __restrict__ cols, const T* __restrict__ vals, int len, int cap,
                                       const X* __restrict__ x) {
-  // up to 16 entries at a time: their index and value loads are all issued, then their
-  // gathers, then the products are summed in entry order
   constexpr int U = 4;
   X acc = 0;
-  for (int q0 = 0; q0 < len; q0 += 4 * U) {
+  int q0 = 0;
+  do {
     int4 c[U];
     Vec4<T> v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       c[u] = make_int4(0, 0, 0, 0);
-      if (q0 + 4 * u < len) {
+      if (q0 + 4 * u < cap) {
         c[u] = *reinterpret_cast<const int4*>(cols + q0 + 4 * u);
         v[u].load(vals + q0 + 4 * u);
       }
@@ -75,25 +76,20 @@ __device__ __forceinline__ X slot_dot(const int* __restrict__ cols, const T* __r
 #pragma unroll
       for (int k = 0; k < 4; ++k)
         if (q0 + 4 * u + k < len) acc += (X)v[u].v[k] * xv[4 * u + k];
-  }
+    q0 += 4 * U;
+  } while (q0 < len);
   return acc;
 }
 
-// y = A_p x, one row per thread; the next row's slot and length are fetched while
-// the current row is summed.
+// y = A_p x: one particle's slot per thread, taken in slot order (consecutive threads
+// read consecutive slots), the result scattered to the slot's row of A_p.
 template <typename T>
 __device__ __forceinline__ void spmv(const Walker& w, const T* __restrict__ x, T* __restrict__ y) {
   const T* av = a_vals<T>(w);
   const int n = w.n, cap = w.cap, nt = blockDim.x;
-  int r = threadIdx.x;
-  int p = r < n ? w.part_of_row[r] : 0;
-  int len = r < n ? w.a_len[p] : 0;
-  for (; r < n; r += nt) {
-    const int rn = r + nt;
-    const int pn = rn < n ? w.part_of_row[rn] : 0;
-    y[r] = slot_dot<T, T>(w.a_col + (size_t)p * cap, av + (size_t)p * cap, len, x);
-    len = rn < n ? w.a_len[pn] : 0;
-    p = pn;
+  for (int p = threadIdx.x; p < n; p += nt) {
+    const int len = w.a_len[p], r = w.row_of_part[p];
+    y[r] = slot_dot<T, T>(w.a_col + (size_t)p * cap, av + (size_t)p * cap, len, cap, x);
   }
 }
 
@@ -194,9 +190,9 @@ __device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, boo
           int r = 0;
           if (on) {
             r = rws[i];
+            T part2 = 0;
             const int e = st[i + 1];
             int t = st[i] + gl;
-            T part2 = 0;
             for (; t + G < e; t += 2 * G) {  // two entries in flight per lane
               part += vl[t] * y[cl[t]];
               part2 += vl[t + G] * y[cl[t + G]];
@@ -567,20 +563,14 @@ __device__ __forceinline__ double residual64(const Walker& w, int brow, double* 
   const int n = w.n, cap = w.cap, nt = blockDim.x;
   const long long t0 = clock64();
   double ss = 0.0, xx = 0.0;
-  int r = threadIdx.x;
-  int p = r < n ? w.part_of_row[r] : 0;
-  int len = r < n ? w.a_len[p] : 0;
-  for (; r < n; r += nt) {
-    const int rn = r + nt;
-    const int pn = rn < n ? w.part_of_row[rn] : 0;
-    const double acc = slot_dot<double, double>(w.a_col + (size_t)p * cap, w.a_val + (size_t)p * cap, len, w.x64);
+  for (int p = threadIdx.x; p < n; p += nt) {  // slots in order (see spmv)
+    const int len = w.a_len[p], r = w.row_of_part[p];
+    const double acc = slot_dot<double, double>(w.a_col + (size_t)p * cap, w.a_val + (size_t)p * cap, len, cap, w.x64);
     const double rr = (r == brow ? 1.0 : 0.0) - acc;
     w.r64[r] = rr;
     ss += rr * rr;
-    const double xr = w.x64[r];
-    xx += xr * xr;
-    len = rn < n ? w.a_len[pn] : 0;
-    p = pn;
+    const double xp = w.x64[p];
+    xx += xp * xp;
   }
   *xnorm = sqrt(block_sum(xx, sh));
   const double rn = sqrt(block_sum(ss, sh));
