@@ -227,6 +227,16 @@ vmc_status vmc_sweep_async(vmc_ctx* ctx, int n_sweeps, double sigma, const uint6
  * walker error. */
 vmc_status vmc_synchronize(vmc_ctx* ctx);
 
+/* Kinetic energy of every walker's current configuration (Sec. 4 Eq. 21, read as
+ *   E = (1/2n) sum_{p,o} (6 kappa - 4 kappa^2 |r_p - Z_o|^2) A_po (A^{-1})_op ,
+ * min-image distances): for each particle p one solve A z = e_p by the engine's
+ * preconditioned GMRES (z = column p of A^{-1}), contracted with p's Slater row
+ * weighted by the Laplacian factor of each Gaussian, refined in FP64 to the solver's
+ * ratio_tol.  energy: host, n_walkers doubles, written before return.  Counts as n
+ * solves per walker in the statistics.  VMC_ERR_INVALID with the dense engine,
+ * VMC_ERR_STATE before positions are set. */
+vmc_status vmc_kinetic_energy(vmc_ctx* ctx, double* energy);
+
 vmc_status vmc_get_stats(vmc_ctx* ctx, int walker, vmc_stats* out);
 vmc_status vmc_reset_stats(vmc_ctx* ctx);
 const char* vmc_last_error(const vmc_ctx* ctx);

@@ -148,6 +148,7 @@ struct vmc_ctx {
   Walker* dWf = nullptr;
   Ctl* dShadow = nullptr;
   int launch_seq = 0;
+  double* d_energy = nullptr;  // kinetic energies, one per walker (in the arena)
   // CUDA graph of one sweep of the STEP / PLAIN engines (replayed once per sweep)
   cudaGraphExec_t graph = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -494,6 +495,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   }
   const size_t ctl_off = cv.take<Ctl>(n_walkers);
   const size_t walk_off = cv.take<Walker>(n_walkers);
+  const size_t energy_off = cv.take<double>(n_walkers);
   const size_t shadow_off = ctx->pair ? cv.take<Ctl>(n_walkers) : 0;
   const size_t walk1_off = ctx->pair ? cv.take<Walker>(n_walkers) : 0;
   const size_t walkf_off = ctx->pair ? cv.take<Walker>(2 * (size_t)n_walkers) : 0;
@@ -505,6 +507,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   char* A = ctx->arena;
   ctx->dCtl = (Ctl*)(A + ctl_off);
   ctx->dW = (Walker*)(A + walk_off);
+  ctx->d_energy = (double*)(A + energy_off);
   for (int w = 0; w < n_walkers; ++w) {
     const auto& o = offs[w];
     Walker& W = ctx->hw[w];
@@ -745,6 +748,16 @@ extern "C" vmc_status vmc_ratio(vmc_ctx* ctx, int walker, int k, const double r_
   *ratio = h.pend_ratio;
   ctx->pending[walker] = 1;
   return VMC_OK;
+}
+
+extern "C" vmc_status vmc_kinetic_energy(vmc_ctx* ctx, double* energy) {
+  if (ctx && ctx->dense) return fail(ctx, VMC_ERR_INVALID, "not available with the dense engine");
+  if (!ctx || !energy) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  if (!ctx->ready) return fail(ctx, VMC_ERR_STATE, "positions not set");
+  CK(launch_kinetic(cfg(ctx), ctx->dW, ctx->nw, ctx->P, ctx->d_energy), "kinetic-energy kernel");
+  CK(cudaMemcpyAsync(energy, ctx->d_energy, sizeof(double) * ctx->nw, cudaMemcpyDeviceToHost, ctx->stream), "energy");
+  for (int w = 0; w < ctx->nw; ++w) ctx->pending[w] = 0;
+  return check_walker_status(ctx);
 }
 
 extern "C" vmc_status vmc_accept(vmc_ctx* ctx, int walker) {

@@ -499,6 +499,39 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_accept(const Walker* __restr
   if (threadIdx.x == 0) { c->pend_valid = 0; c->accepts += 1; }
 }
 
+// Kinetic energy (Sec. 4 Eq. 21, read as (1/2n) sum_{p,o} (6 kappa - 4 kappa^2 |r_p - Z_o|^2)
+// A_po (A^{-1})_op).  For every particle p the solve of a ratio, A z = e_p (z = column p
+// of A^{-1}, indexed by orbital), contracted with the particle's own Slater row weighted by
+// the Laplacian factor of each Gaussian; the weighted row takes the place of u, so the FP64
+// refinement controls the error of this contraction.  One CTA per walker; out[walker].
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads, 2) k_kinetic(const Walker* __restrict__ W, Params P, double* out) {
+  __shared__ Shared sh;
+  ring_init(sh, P);
+  const Walker& w = active_of(W[blockIdx.x]);
+  const int n = w.n, cap = w.cap;
+  const double kap = w.kappa;
+  double e = 0.0;
+  for (int k = 0; k < n; ++k) {
+    if (w.ctl->status != ST_OK) break;  // read by every thread after the last barrier
+    const int len = w.a_len[k];
+    const double rk[3] = {w.R[3 * k], w.R[3 * k + 1], w.R[3 * k + 2]};
+    for (int t = threadIdx.x; t < len; t += blockDim.x) {
+      const int col = w.a_col[(size_t)k * cap + t];
+      const double d2 = dist2(rk, w.Z + 3 * w.orb_of_col[col], w.L);
+      sh.ucol[t] = col;
+      sh.uval[t] = (6.0 * kap - 4.0 * kap * kap * d2) * w.a_val[(size_t)k * cap + t];
+    }
+    if (threadIdx.x == 0) sh.ulen = len;
+    __syncthreads();
+    SolveOut o;
+    solve_with_controller<T>(w, P, k, o, sh);
+    if (threadIdx.x == 0) e += o.ratio - 1.0;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = e / (2.0 * n);
+}
+
 // r = wrap(Z + jitter * N(0,1)^3), purpose 0, sweep 0.
 __global__ void k_init_positions(const Walker* __restrict__ W, const uint64_t* __restrict__ seeds, double jitter) {
   const Walker& w = W[blockIdx.x];
@@ -700,6 +733,10 @@ cudaError_t launch_step(const LaunchCfg& L, const Walker* W, int walker0, int nw
 cudaError_t launch_ratio(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int k, const double r[3]) {
   if (L.fp64) VMC_LAUNCH(k_ratio<double>, 1, W, wi, P, k, r[0], r[1], r[2]);
   VMC_LAUNCH(k_ratio<float>, 1, W, wi, P, k, r[0], r[1], r[2]);
+}
+cudaError_t launch_kinetic(const LaunchCfg& L, const Walker* W, int nwalk, const Params& P, double* out) {
+  if (L.fp64) VMC_LAUNCH(k_kinetic<double>, nwalk, W, P, out);
+  VMC_LAUNCH(k_kinetic<float>, nwalk, W, P, out);
 }
 cudaError_t launch_accept(const LaunchCfg& L, const Walker* W, int wi, const Params& P) {
   if (L.fp64) VMC_LAUNCH(k_accept<double>, 1, W, wi, P);

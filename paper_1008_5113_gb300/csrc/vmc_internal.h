@@ -36,6 +36,8 @@ cudaError_t launch_set_sweep(long long* sweep_dev, long long v, cudaStream_t s);
 cudaError_t prepare_step_kernels(const LaunchCfg& L);
 cudaError_t launch_ratio(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int k, const double r[3]);
 cudaError_t launch_accept(const LaunchCfg& L, const Walker* W, int wi, const Params& P);
+// Kinetic energy of every walker into out[0 .. nwalk) (device).
+cudaError_t launch_kinetic(const LaunchCfg& L, const Walker* W, int nwalk, const Params& P, double* out);
 cudaError_t launch_init_positions(const LaunchCfg& L, const Walker* W, int nwalk, const uint64_t* seeds, double jitter);
 cudaError_t launch_setup(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P);
 cudaError_t launch_refactor(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int reorder);

@@ -82,6 +82,7 @@ _SIG = {
     "vmc_sweep": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vmc_sweep_async": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vmc_synchronize": (C.c_int, [C.c_void_p]),
+    "vmc_kinetic_energy": (C.c_int, [C.c_void_p, C.c_void_p]),
     "vmc_get_stats": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "vmc_reset_stats": (C.c_int, [C.c_void_p]),
     "vmc_last_error": (C.c_char_p, [C.c_void_p]),
@@ -215,6 +216,12 @@ def vmc_sweep_async(ctx, n_sweeps: int, sigma: float, seeds_dev, accept_log_dev=
 
 def vmc_synchronize(ctx) -> None:
     _check(lib().vmc_synchronize(ctx), ctx)
+
+
+def vmc_kinetic_energy(ctx, n_walkers: int) -> np.ndarray:
+    e = np.zeros(n_walkers)
+    _check(lib().vmc_kinetic_energy(ctx, _p(e)), ctx)
+    return e
 
 
 def vmc_get_stats(ctx, walker: int) -> dict:

@@ -8,6 +8,7 @@ their inputs from these parameters; neither imports the other.
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass, field
 
 
@@ -54,4 +55,14 @@ UNEVEN_320 = Workload("sc8-20_uneven_w320_mixed", (8, 10, 12, 16, 20), 64, 10, p
 LARGE_32768 = Workload("sc32_n32768_k1_rc2_w32_mixed", (32,), 32, 5, kappa=1.0, r_c=2.0, sigma=0.25,
                        precision="mixed")
 
-ALL = [PLAIN_216, BATCH_1000, MIXED_4096, UNEVEN_320, LARGE_32768]
+# The paper's own model system (Sec. 4): body-centred cubic lattice of cube side 2.031,
+# kappa = 1, matrix entries below 1e-5 of the largest (1, at a site) dropped -- read as the
+# cutoff r_c = sqrt(5 ln 10 / kappa) -- n = 2 K^3 (K = 7: n = 686, the paper's smallest);
+# start jitter and step scale with the cube side (0.1 a, 0.2 a)
+PAPER_BCC = Workload("bcc_a2.031_k1_n686_paper", (7,), 1, 10, kappa=1.0, r_c=math.sqrt(5.0 * math.log(10.0)),
+                     a=2.031, lattice=1, jitter=0.2031, sigma=0.4062)
+# the paper's solver settings (Sec. 4): ILUTP drop 0.01, column-pivot tolerance 0.05,
+# lfil half the average row count (the default), GMRES up to 40 iterations to 1e-6
+PAPER_SOLVER = dict(drop_tol=0.01, permtol=0.05, gmres_m=40, inner_rtol=1e-6)
+
+ALL = [PLAIN_216, BATCH_1000, MIXED_4096, UNEVEN_320, LARGE_32768, PAPER_BCC]

@@ -182,3 +182,52 @@ def test_dense_engine_matches_oracle(vmc):
     _, r_ref, a_ref, u_ref = O.chain(s, 1, wl.sigma, R0, 3, solver=O.SOLVER_DENSE_LU)
     assert compare_chain(rat, acc, r_ref, a_ref, u_ref) > 400
     assert st["factorizations"] == 3 and st["status"] == 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_paper_bcc_workload_matches_oracle(vmc, prec):
+    """The paper's own model (bcc, cube side 2.031, kappa 1, entries < 1e-5 dropped) with its
+    solver settings (ILUTP 0.01 / 0.05, GMRES 40 to 1e-6), at K = 5 (n = 250): the FP64
+    refinement keeps the ratios at the oracle's."""
+    wl = WL.PAPER_BCC
+    K = 5
+    sysw = (K, 1, wl.a, wl.kappa, wl.r_c)
+    ctx = vmc.vmc_create([sysw], vmc.params(precision=0 if prec == "fp64" else 1, **WL.PAPER_SOLVER))
+    try:
+        vmc.vmc_init_positions(ctx, [1], wl.jitter)
+        acc, rat = vmc.vmc_sweep(ctx, 2, wl.sigma, [1])
+        st = vmc.vmc_get_stats(ctx, 0)
+    finally:
+        vmc.vmc_destroy(ctx)
+    s = O.system(K, 1, wl.a, wl.kappa, wl.r_c)
+    R0 = O.initial_positions(s, 1, wl.jitter)
+    _, r_ref, a_ref, u_ref = O.chain(s, 1, wl.sigma, R0, 2, solver=O.SOLVER_DENSE_LU)
+    assert compare_chain(rat, acc, r_ref, a_ref, u_ref) > 200
+    assert st["status"] == 0 and st["proposals"] == 500
+    assert 30 <= st["nnz_A"] / 250 <= 60  # rows of the truncated Gaussians (about 42 in the paper)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_kinetic_energy_matches_oracle(vmc, prec):
+    """Eq. 21 on the device (n preconditioned solves per walker) against the oracle's
+    dense evaluation, at the start and after a sweep, for a simple-cubic and the paper's
+    bcc system."""
+    wl, bcc = WL.PLAIN_216, WL.PAPER_BCC
+    systems = [(6, 0, wl.a, wl.kappa, wl.r_c), (4, 1, bcc.a, bcc.kappa, bcc.r_c)]
+    jit = [wl.jitter, bcc.jitter]
+    ctx = vmc.vmc_create(systems, vmc.params(precision=0 if prec == "fp64" else 1))
+    try:
+        for w, sysw in enumerate(systems):
+            s = O.system(*sysw)
+            vmc.vmc_set_positions(ctx, w, O.initial_positions(s, w + 1, jit[w]))
+        for sweep in range(2):
+            e = vmc.vmc_kinetic_energy(ctx, 2)
+            for w, sysw in enumerate(systems):
+                s = O.system(*sysw)
+                ref = O.kinetic_energy(s, O.sites(s), vmc.vmc_get_positions(ctx, w))
+                assert abs(e[w] - ref) <= 1e-10 * abs(ref), (sweep, w, e[w], ref)
+            vmc.vmc_sweep(ctx, 1, 0.2, [1, 2])
+        st = vmc.vmc_get_stats(ctx, 0)
+        assert st["status"] == 0 and st["solves"] >= 2 * 216
+    finally:
+        vmc.vmc_destroy(ctx)
