@@ -306,6 +306,13 @@ def main():
         sm = [vmc.vmc_get_stats(ctxm, w) for w in range(WALKERS)]
         extra["mixed_value"] = sum(s["proposals"] for s in sm) / (tm / 1000.0)
         vmc.vmc_destroy(ctxm)
+        # ---- the dense reference point: explicit inverse + Sherman-Morrison (Sec. 1), FP64,
+        #      same walkers and sweeps, a fresh inverse every sweep -------------------------
+        ctxd = make(vmc.PREC_FP64, vmc.ENGINE_DENSE_SM)
+        td, _, _ = timed_sweeps(ctxd, args.steps, args.warmup)
+        sd_ = [vmc.vmc_get_stats(ctxd, w) for w in range(WALKERS)]
+        extra["dense_sm_fp64_value"] = sum(x["proposals"] for x in sd_) / (td / 1000.0)
+        vmc.vmc_destroy(ctxd)
         # ---- plain FP64 one-walker-per-launch path (bounded sample: 1 walker, 1 sweep) ---
         # started from walker 0's configuration at the first timed sweep, with that sweep's
         # random numbers, so that both paths solve equally conditioned matrices
@@ -329,13 +336,14 @@ def main():
             extra["speedup_vs_plain"] = value / plain
             extra["speedup_vs_plain_mixed"] = extra["mixed_value"] / plain
     if rank == 0 and not args.no_kernels:
-        # ---- per-kernel rooflines at the HBM-sized configurations (CTA per walker, 152
-        #      walkers = one per SM): triangular solves and SpMV, FP32 (mixed mode) -----
+        # ---- per-kernel rooflines at the HBM-sized configurations (CTA per walker; n = 4096
+        #      with 256 walkers, n = 32768 with 152 = one per SM): triangular solves and SpMV,
+        #      FP32 (mixed mode) ------------------------------------------------------------
         hbm_peak, _ = peaks()
         kr = {}
-        for K in (16, 32):
-            ctxk = vmc.vmc_create([(K, 0, A, KAPPA, RC)] * 152, vmc.params(precision=vmc.PREC_MIXED), stream=stream)
-            vmc.vmc_init_positions(ctxk, list(range(1, 153)), JITTER)
+        for K, nwk in ((16, 256), (32, 152)):  # n = 4096 with its configuration's 256 walkers
+            ctxk = vmc.vmc_create([(K, 0, A, KAPPA, RC)] * nwk, vmc.params(precision=vmc.PREC_MIXED), stream=stream)
+            vmc.vmc_init_positions(ctxk, list(range(1, nwk + 1)), JITTER)
             reps = 40 if K == 16 else 10
             for which, name in ((0, "trisolve"), (1, "spmv")):
                 vmc.vmc_kernel_bench(ctxk, which, 2)
@@ -349,9 +357,9 @@ def main():
                 torch.cuda.synchronize()
                 vmc.vmc_synchronize(ctxk)
                 ms = e0.elapsed_time(e1)
-                by = sum(vmc.vmc_get_stats(ctxk, w)["alg_bytes"] for w in range(152))
+                by = sum(vmc.vmc_get_stats(ctxk, w)["alg_bytes"] for w in range(nwk))
                 gbs = by / (ms / 1000.0) / 1e9
-                kr[f"{name}_sc{K}_n{K ** 3}_w152_f32"] = {
+                kr[f"{name}_sc{K}_n{K ** 3}_w{nwk}_f32"] = {
                     "us_per_apply": 1000.0 * ms / reps, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": gbs / hbm_peak, "bytes_per_apply": by / reps}
             vmc.vmc_destroy(ctxk)
