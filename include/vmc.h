@@ -207,6 +207,15 @@ int vmc_walker_n(const vmc_ctx* ctx, int walker);
  * doubles; wrapped into the box).  Nothing is committed; the solve is kept so that
  * vmc_accept can commit it.  Sec. 3 Eq. 13. */
 vmc_status vmc_ratio(vmc_ctx* ctx, int walker, int k, const double r_new[3], double* ratio);
+/* vmc_ratio plus the quantities of a drift-diffusion step at the proposed position
+ * (Sec. 2.2; the same solve: column k of A'^{-1} is A^{-1} e_k / ratio):
+ *   grad = grad_{r'} ln|det A'|   (host, 3 doubles; nullable)
+ *   lap  = lap_{r'} det A' / det A'   (host; nullable)
+ * with grad phi = -2 kappa (r' - Z) phi and lap phi = (4 kappa^2 |r' - Z|^2 - 6 kappa) phi
+ * (minimum image).  Accurate to the solve's tolerance; the refinement targets the ratio.
+ * The move stays pending for vmc_accept as with vmc_ratio. */
+vmc_status vmc_ratio_grad(vmc_ctx* ctx, int walker, int k, const double r_new[3], double* ratio, double grad[3],
+                          double* lap);
 /* Commit the move of the last vmc_ratio on walker w: replace the Slater row and
  * apply the rank-one preconditioner update (Sec. 3.2 Eq. 17).  VMC_ERR_STATE if
  * no ratio is pending. */

@@ -78,6 +78,7 @@ def lib():
                 "orc_chains": (C.c_long, [sp, i, p, d, i, i, C.c_long, i, i, p, p, p, i]),
                 "orc_max_threads": (i, []),
                 "orc_kinetic_energy": (d, [sp, p, p]),
+                "orc_ratio_grad_lap": (i, [sp, p, p, i, p, p, p, p]),
                 "orc_greedy_pairing": (None, [sp, p, p, p, p]),
             }
             for name, (res, args) in sig.items():
@@ -289,3 +290,16 @@ def greedy_pairing(s: System, R: np.ndarray, Z: np.ndarray, P, Q):
 def kinetic_energy(s: System, Z: np.ndarray, R: np.ndarray) -> float:
     """Kinetic-energy estimator of Eq. 21 (hbar = mass = 1)."""
     return lib().orc_kinetic_energy(C.byref(s), _ptr(Z), _ptr(np.ascontiguousarray(R)))
+
+
+def ratio_grad_lap(s: System, Z: np.ndarray, R: np.ndarray, i: int, r_new):
+    """(ratio, grad ln|det A'| at r_new, lap det A' / det A' at r_new) for moving particle i."""
+    rn = np.ascontiguousarray(r_new, dtype=np.float64)
+    ratio = C.c_double(0.0)
+    g = np.zeros(3)
+    lap = C.c_double(0.0)
+    rc = lib().orc_ratio_grad_lap(C.byref(s), _ptr(Z), _ptr(np.ascontiguousarray(R)), int(i), _ptr(rn),
+                                  C.byref(ratio), _ptr(g), C.byref(lap))
+    if rc:
+        raise RuntimeError("singular Slater matrix")
+    return ratio.value, g, lap.value

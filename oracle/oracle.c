@@ -685,3 +685,59 @@ double orc_kinetic_energy(const orc_system* s, const double* Z, const double* R)
   free(A); free(B);
   return E;
 }
+
+/* ======================================================================== */
+/* Gradient and Laplacian at a proposed position (quantities of the drift   */
+/* and the local energy, Sec. 2.2).  With A' = A with row i replaced by      */
+/* a(r'), column i of A'^{-1} is z / ratio, z = A^{-1} e_i, so               */
+/*   grad = sum_o grad phi_o(r') z_o / ratio  = grad_{r'} ln|det A'|,        */
+/*   lap  = sum_o lap phi_o(r') z_o / ratio   = lap_{r'} det A' / det A',    */
+/* grad phi = -2k (r - Z) phi, lap phi = (4k^2 d^2 - 6k) phi (min image).    */
+/* Dense LU for z.  Returns nonzero if A is singular.                        */
+/* ======================================================================== */
+int orc_ratio_grad_lap(const orc_system* s, const double* Z, const double* R, int i, const double r_new[3],
+                       double* ratio, double grad[3], double* lap) {
+  int n = orc_n(s);
+  size_t nn = (size_t)n * n;
+  double L = box_len(s);
+  double rc2 = s->r_c * s->r_c;
+  double* A = (double*)malloc(sizeof(double) * nn);
+  double* e = (double*)calloc((size_t)n, sizeof(double));
+  double* z = (double*)malloc(sizeof(double) * n);
+  double* a = (double*)malloc(sizeof(double) * n);
+  int* piv = (int*)malloc(sizeof(int) * n);
+  int sign, rc = 0;
+  orc_slater_dense(s, Z, R, A);
+  orc_row_dense(s, Z, r_new, a);
+  {
+    double acc = 0.0; /* u^T z needs the old row: take it before factoring */
+    double* Acopy = (double*)malloc(sizeof(double) * nn);
+    memcpy(Acopy, A, sizeof(double) * nn);
+    if (orc_lu(n, A, piv, &sign)) {
+      rc = 1;
+    } else {
+      e[i] = 1.0;
+      orc_lu_solve(n, A, piv, e, z);
+      for (int j = 0; j < n; ++j) acc += (a[j] - Acopy[(size_t)i * n + j]) * z[j];
+      *ratio = 1.0 + acc;
+      double g[3] = {0.0, 0.0, 0.0}, l = 0.0;
+      for (int o = 0; o < n; ++o) {
+        double dx = min_image(r_new[0] - Z[3 * o + 0], L);
+        double dy = min_image(r_new[1] - Z[3 * o + 1], L);
+        double dz = min_image(r_new[2] - Z[3 * o + 2], L);
+        double d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 > rc2) continue;
+        double ph = exp(-s->kappa * d2);
+        g[0] += -2.0 * s->kappa * dx * ph * z[o];
+        g[1] += -2.0 * s->kappa * dy * ph * z[o];
+        g[2] += -2.0 * s->kappa * dz * ph * z[o];
+        l += (4.0 * s->kappa * s->kappa * d2 - 6.0 * s->kappa) * ph * z[o];
+      }
+      for (int d = 0; d < 3; ++d) grad[d] = g[d] / *ratio;
+      *lap = l / *ratio;
+    }
+    free(Acopy);
+  }
+  free(A); free(e); free(z); free(a); free(piv);
+  return rc;
+}

@@ -15,6 +15,7 @@
  *   - det ratio = 1 + u^T A^{-1} e_i                                   (Eq. 2 of Sec. 1 / Eq. 13, Sec. 3)
  *   - the standard algorithm: explicit inverse + Sherman-Morrison      (Sec. 1)
  *   - kinetic-energy estimator                                         (Eq. 21, Sec. 4)
+ *   - gradient and Laplacian of det at a proposed position             (Sec. 2.2)
  * The random numbers are Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
  * written here from its published definition, with Box-Muller normals.
  *
@@ -115,6 +116,12 @@ void orc_greedy_pairing(const orc_system* s, const double* R, const double* Z, i
 
 /* ---- kinetic energy (Eq. 21): (1/2n) sum_{p,o} (6k - 4k^2 |r_p - Z_o|^2) A_po (A^-1)_op */
 double orc_kinetic_energy(const orc_system* s, const double* Z, const double* R);
+
+/* ---- gradient and Laplacian at a proposed position (drift and local energy, Sec. 2.2):
+ * ratio as orc_ratio_dense; grad = grad_{r'} ln|det A'|, lap = lap_{r'} det A' / det A',
+ * A' = A with row i replaced by the row at r_new.  Nonzero return: A singular. */
+int orc_ratio_grad_lap(const orc_system* s, const double* Z, const double* R, int i, const double r_new[3],
+                       double* ratio, double grad[3], double* lap);
 
 #ifdef __cplusplus
 }

@@ -731,7 +731,8 @@ extern "C" vmc_status vmc_get_positions(vmc_ctx* ctx, int walker, double* xyz) {
   return VMC_OK;
 }
 
-extern "C" vmc_status vmc_ratio(vmc_ctx* ctx, int walker, int k, const double r_new[3], double* ratio) {
+static vmc_status ratio_impl(vmc_ctx* ctx, int walker, int k, const double r_new[3], double* ratio, double* grad,
+                             double* lap) {
   if (ctx && ctx->dense) return fail(ctx, VMC_ERR_INVALID, "not available with the dense engine");
   if (!ctx || !r_new || !ratio || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
   if (!ctx->ready) return fail(ctx, VMC_ERR_STATE, "positions not set");
@@ -739,15 +740,28 @@ extern "C" vmc_status vmc_ratio(vmc_ctx* ctx, int walker, int k, const double r_
   if (k < 0 || k >= W.n) return fail(ctx, VMC_ERR_INVALID, "particle index out of range");
   for (int d = 0; d < 3; ++d)
     if (!std::isfinite(r_new[d])) return fail(ctx, VMC_ERR_INVALID, "non-finite position");
-  CK(launch_ratio(cfg(ctx), ctx->dW, walker, ctx->P, k, r_new), "ratio kernel");
+  const bool want = grad || lap;
+  CK(launch_ratio(cfg(ctx), ctx->dW, walker, ctx->P, k, r_new, want ? 1 : 0), "ratio kernel");
   Ctl h;
   CK(cudaMemcpyAsync(&h, ctx->dCtl + walker, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream), "read ratio");
   CK(cudaStreamSynchronize(ctx->stream), "synchronize");
   if (h.status != ST_OK) return fail(ctx, (vmc_status)h.status, "walker failed with status " + std::to_string(h.status));
   if (!h.pend_valid) { ctx->pending[walker] = 0; return fail(ctx, VMC_ERR_NOCONV, "solve did not converge"); }
   *ratio = h.pend_ratio;
+  if (grad)
+    for (int d = 0; d < 3; ++d) grad[d] = h.pend_grad[d];
+  if (lap) *lap = h.pend_lap;
   ctx->pending[walker] = 1;
   return VMC_OK;
+}
+
+extern "C" vmc_status vmc_ratio(vmc_ctx* ctx, int walker, int k, const double r_new[3], double* ratio) {
+  return ratio_impl(ctx, walker, k, r_new, ratio, nullptr, nullptr);
+}
+
+extern "C" vmc_status vmc_ratio_grad(vmc_ctx* ctx, int walker, int k, const double r_new[3], double* ratio,
+                                     double grad[3], double* lap) {
+  return ratio_impl(ctx, walker, k, r_new, ratio, grad, lap);
 }
 
 extern "C" vmc_status vmc_kinetic_energy(vmc_ctx* ctx, double* energy) {

@@ -58,6 +58,7 @@ struct Ctl {
   int nchunk_l, nchunk_u;
   double pend_r[3];
   double pend_ratio;
+  double pend_grad[3], pend_lap;  // gradient / Laplacian at the pending position (when asked)
   double its_sum;
   long long its_cnt;
   long long proposals, accepts, solves, inner_its, first_its, outer_passes;

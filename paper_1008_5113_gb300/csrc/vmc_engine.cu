@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_step(const Walker* __restric
 // Single-move API: ratio for particle k moved to r_new (no commit); result in ctl.
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads, 2) k_ratio(const Walker* __restrict__ W, int wi, Params P, int k, double rx,
-                                                double ry, double rz) {
+                                                double ry, double rz, int want_grad) {
   __shared__ Shared sh;
   ring_init(sh, P);
   const Walker& w = active_of(W[wi]);
@@ -465,6 +465,29 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_ratio(const Walker* __restri
   if (!build_move(w, k, sh)) return;
   SolveOut o;
   solve_with_controller<T>(w, P, k, o, sh);
+  if (want_grad) {
+    // column k of A'^{-1} is z / ratio (z = A^{-1} e_k, in x64), so at r':
+    // grad ln|det A'| = sum_o grad phi_o(r') z_o / ratio with grad phi = -2 kappa (r' - Z_o) phi,
+    // lap det A' / det A' = sum_o (4 kappa^2 d^2 - 6 kappa) phi z_o / ratio
+    double g[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int t = threadIdx.x; t < sh.alen; t += blockDim.x) {
+      const int col = sh.acol[t];
+      const double* zo = w.Z + 3 * w.orb_of_col[col];
+      const double dx = min_image(__dsub_rn(sh.rnew[0], zo[0]), w.L);
+      const double dy = min_image(__dsub_rn(sh.rnew[1], zo[1]), w.L);
+      const double dz = min_image(__dsub_rn(sh.rnew[2], zo[2]), w.L);
+      const double pz = sh.aval[t] * w.x64[col];
+      g[0] += -2.0 * w.kappa * dx * pz;
+      g[1] += -2.0 * w.kappa * dy * pz;
+      g[2] += -2.0 * w.kappa * dz * pz;
+      g[3] += (4.0 * w.kappa * w.kappa * (dx * dx + dy * dy + dz * dz) - 6.0 * w.kappa) * pz;
+    }
+    for (int d = 0; d < 4; ++d) g[d] = block_sum(g[d], sh);
+    if (threadIdx.x == 0) {
+      for (int d = 0; d < 3; ++d) c->pend_grad[d] = g[d] / o.ratio;
+      c->pend_lap = g[3] / o.ratio;
+    }
+  }
   for (int t = threadIdx.x; t < sh.alen; t += blockDim.x) { w.pend_acol[t] = sh.acol[t]; w.pend_aval[t] = sh.aval[t]; }
   for (int t = threadIdx.x; t < sh.ulen; t += blockDim.x) { w.pend_ucol[t] = sh.ucol[t]; w.pend_uval[t] = sh.uval[t]; }
   if (threadIdx.x == 0) {
@@ -730,9 +753,10 @@ cudaError_t launch_step(const LaunchCfg& L, const Walker* W, int walker0, int nw
                          sweep_dev);
   VMC_LAUNCH(k_step<float>, nwalk, W, walker0, P, q, n_sweeps, s_local, sweep0, sigma, seeds, acc, ratio, sweep_dev);
 }
-cudaError_t launch_ratio(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int k, const double r[3]) {
-  if (L.fp64) VMC_LAUNCH(k_ratio<double>, 1, W, wi, P, k, r[0], r[1], r[2]);
-  VMC_LAUNCH(k_ratio<float>, 1, W, wi, P, k, r[0], r[1], r[2]);
+cudaError_t launch_ratio(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int k, const double r[3],
+                         int want_grad) {
+  if (L.fp64) VMC_LAUNCH(k_ratio<double>, 1, W, wi, P, k, r[0], r[1], r[2], want_grad);
+  VMC_LAUNCH(k_ratio<float>, 1, W, wi, P, k, r[0], r[1], r[2], want_grad);
 }
 cudaError_t launch_kinetic(const LaunchCfg& L, const Walker* W, int nwalk, const Params& P, double* out) {
   if (L.fp64) VMC_LAUNCH(k_kinetic<double>, nwalk, W, P, out);

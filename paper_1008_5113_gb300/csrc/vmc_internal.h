@@ -34,7 +34,9 @@ cudaError_t launch_next_sweep(long long* sweep_dev, cudaStream_t s);
 cudaError_t launch_set_sweep(long long* sweep_dev, long long v, cudaStream_t s);
 // Sets the step kernels' shared-memory attribute (before a graph capture).
 cudaError_t prepare_step_kernels(const LaunchCfg& L);
-cudaError_t launch_ratio(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int k, const double r[3]);
+// want_grad: also the gradient and Laplacian at r (Ctl::pend_grad, pend_lap)
+cudaError_t launch_ratio(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int k, const double r[3],
+                         int want_grad = 0);
 cudaError_t launch_accept(const LaunchCfg& L, const Walker* W, int wi, const Params& P);
 // Kinetic energy of every walker into out[0 .. nwalk) (device).
 cudaError_t launch_kinetic(const LaunchCfg& L, const Walker* W, int nwalk, const Params& P, double* out);

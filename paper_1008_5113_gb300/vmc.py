@@ -79,6 +79,7 @@ _SIG = {
     "vmc_walker_n": (C.c_int, [C.c_void_p, C.c_int]),
     "vmc_ratio": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "vmc_accept": (C.c_int, [C.c_void_p, C.c_int]),
+    "vmc_ratio_grad": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vmc_sweep": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vmc_sweep_async": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vmc_synchronize": (C.c_int, [C.c_void_p]),
@@ -193,6 +194,16 @@ def vmc_ratio(ctx, walker: int, k: int, r_new) -> float:
     out = C.c_double(0.0)
     _check(lib().vmc_ratio(ctx, walker, k, _p(r), C.byref(out)), ctx)
     return out.value
+
+
+def vmc_ratio_grad(ctx, walker: int, k: int, r_new):
+    """(ratio, grad ln|det A'|, lap det A' / det A') at the proposed position."""
+    r = np.ascontiguousarray(r_new, dtype=np.float64)
+    out = C.c_double(0.0)
+    g = np.zeros(3)
+    lap = C.c_double(0.0)
+    _check(lib().vmc_ratio_grad(ctx, walker, k, _p(r), C.byref(out), _p(g), C.byref(lap)), ctx)
+    return out.value, g, lap.value
 
 
 def vmc_accept(ctx, walker: int) -> None:

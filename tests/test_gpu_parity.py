@@ -231,3 +231,28 @@ def test_kinetic_energy_matches_oracle(vmc, prec):
         assert st["status"] == 0 and st["solves"] >= 2 * 216
     finally:
         vmc.vmc_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ratio_gradient_and_laplacian_match_oracle(vmc, prec):
+    """Drift and local-energy quantities at proposed positions (the same solve as the
+    ratio), through the single-move API, accepting every other move."""
+    K, seed = 6, 4
+    s = O.system(K)
+    Z = O.sites(s)
+    R = O.initial_positions(s, seed, 0.1)
+    ctx = vmc.vmc_create([(K, 0, 1.0, 2.0, 1.5)], vmc.params(precision=0 if prec == "fp64" else 1))
+    try:
+        vmc.vmc_set_positions(ctx, 0, R)
+        for step, k in enumerate([3, 50, 100, 3, 215, 77]):
+            r_new = O.propose(s, 5, step, k, 0.25, R[k])
+            ref, gref, lref = O.ratio_grad_lap(s, Z, R, k, r_new)
+            got, g, lap = vmc.vmc_ratio_grad(ctx, 0, k, r_new)
+            assert abs(got - ref) <= 1e-10 * max(abs(ref), 1e-3)
+            assert np.abs(g - gref).max() <= 1e-9 * max(1.0, np.abs(gref).max())
+            assert abs(lap - lref) <= 1e-9 * max(1.0, abs(lref))
+            if step % 2 == 0:
+                vmc.vmc_accept(ctx, 0)
+                R[k] = r_new
+    finally:
+        vmc.vmc_destroy(ctx)
