@@ -394,6 +394,17 @@ __device__ __noinline__ void precond_apply(const Walker& w, const Params& P, con
       for (int o = G >> 1; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
       if (s_ < mu && gl == 0) sh.cupd[s_] = acc;
     }
+    // G[t][s] (t > s) for the substitution, staged in the idle stream ring when it fits
+    // (the ring's last writer was the bulk-copy proxy: order the generic stores after it)
+    double* Gs = nullptr;
+    if ((size_t)mu * mu * sizeof(double) <= (size_t)P.ring_slots * P.slot_bytes) {
+      Gs = reinterpret_cast<double*>(dyn_smem() + P.y_bytes);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      for (int idx = tid; idx < mu * mu; idx += nt) {
+        const int t = idx / mu, s2 = idx - t * mu;
+        Gs[idx] = s2 < t ? w.upd_G[(size_t)t * kMaxUpd + s2] : 0.0;
+      }
+    }
     __syncthreads();
     // c_s = d_s - sum_{t<s} G[s][t] c_t: warp 0, lane t holds d_t for t = lane + 32 k;
     // each solved c_s is broadcast and subtracted from the later d_t
@@ -406,13 +417,14 @@ __device__ __noinline__ void precond_apply(const Walker& w, const Params& P, con
 #pragma unroll
         for (int k = 0; k < kMaxUpd / 32; ++k) {
           const int t = lane + 32 * k;
-          if (t > s_ && t < mu) d[k] -= w.upd_G[(size_t)t * kMaxUpd + s_] * cs;
+          if (t > s_ && t < mu) d[k] -= (Gs ? Gs[t * mu + s_] : w.upd_G[(size_t)t * kMaxUpd + s_]) * cs;
         }
       }
 #pragma unroll
       for (int k = 0; k < kMaxUpd / 32; ++k)
         if (lane + 32 * k < mu) sh.cupd[lane + 32 * k] = d[k];
     }
+    if (Gs) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // before the ring's next bulk copies
     __syncthreads();
     // w = w_0 - sum_s z_hat_s c_s: row i of Zt is contiguous over s
     for (int i = tid; i < n; i += nt) {
