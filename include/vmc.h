@@ -88,7 +88,8 @@ typedef struct {
   double ratio_tol;    /* goal: predicted relative ratio error (1e-12)                   */
   double N_max;        /* reorder + refactor when the stability monitor N exceeds it (100) */
   double slow_factor;  /* ... or when the iterations reach slow_factor x the average (4)  */
-  int max_updates;     /* refactor after this many rank-one preconditioner updates (64)   */
+  int max_updates;     /* refactor after this many rank-one preconditioner updates; -1 =
+                          auto: 64 with background refactorisation, 128 without (-1)    */
   int precision;       /* VMC_PREC_* (MIXED)                                               */
   int engine;          /* VMC_ENGINE_* (PERSISTENT)                                        */
   int block_threads;   /* threads per walker CTA: 64..256, multiple of 32; 0 = auto (0)  */
@@ -151,6 +152,7 @@ typedef struct {
   int64_t async_factor_cycles; /* factor-CTA cycles spent factoring (off the solver's path) */
   int factor_set;            /* factor set in use (0 or 1)                                  */
   int async_lag;             /* the refactor_lag in effect (0: in-line refactorisation)     */
+  int max_updates;           /* the max_updates in effect                                   */
 } vmc_stats;
 
 /* Fill p with the defaults above. */

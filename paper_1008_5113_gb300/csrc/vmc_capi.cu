@@ -187,7 +187,7 @@ extern "C" vmc_status vmc_default_params(vmc_solver_params* p) {
   p->ratio_tol = 1e-12;
   p->N_max = 100.0;
   p->slow_factor = 4.0;
-  p->max_updates = 64;
+  p->max_updates = -1;
   p->precision = VMC_PREC_MIXED;
   p->engine = VMC_ENGINE_PERSISTENT;
   p->block_threads = 0;
@@ -303,7 +303,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   auto bad = [&](const std::string& m) { ctx->err = m; return VMC_ERR_INVALID; };
   vmc_status st = VMC_OK;
   if (p.gmres_m < 1 || p.gmres_m > kMaxM) st = bad("gmres_m must be in [1, 40]");
-  else if (p.max_updates < 0 || p.max_updates > kMaxUpd) st = bad("max_updates must be in [0, 128]");
+  else if (p.max_updates < -1 || p.max_updates > kMaxUpd) st = bad("max_updates must be -1 or in [0, 128]");
   else if (p.precision != VMC_PREC_FP64 && p.precision != VMC_PREC_MIXED && p.precision != VMC_PREC_MIXED_F32ILU)
     st = bad("precision");
   else if (p.engine < VMC_ENGINE_PLAIN || p.engine > VMC_ENGINE_DENSE_SM) st = bad("engine");
@@ -322,21 +322,24 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   ctx->P.lfil_extra = p.lfil_extra;
   ctx->P.m = p.gmres_m;
   ctx->P.max_restarts = p.max_restarts;
-  ctx->P.max_updates = p.max_updates;
   ctx->P.inner_rtol = p.inner_rtol > 0.0 ? p.inner_rtol : (ctx->fp64 ? 1e-10 : 1e-5);
   ctx->P.ratio_tol = p.ratio_tol > 0.0 ? p.ratio_tol : 1e-12;
   ctx->P.ilu64 = p.precision != VMC_PREC_MIXED_F32ILU;
   ctx->P.N_max = p.N_max;
   ctx->P.slow_factor = p.slow_factor;
   {
-    // background refactorisation (persistent engine): needs a chain of >= 2 updates
+    // background refactorisation (persistent engine) when asked for, or by default when
+    // every walker pair fits; the chain length defaults to 64 with it (adopted every 32
+    // accepts) and to 128 without (in-line refactorisations are the costlier)
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int lag = p.refactor_lag;
-    if (lag < 0) lag = (nsm > 0 && 2 * n_walkers <= nsm) ? p.max_updates / 2 : 0;
-    lag = std::min(lag, p.max_updates / 2);
-    if (p.engine != VMC_ENGINE_PERSISTENT) lag = 0;
+    const bool fits = nsm > 0 && 2 * n_walkers <= nsm;
+    const bool bg = p.engine == VMC_ENGINE_PERSISTENT && (p.refactor_lag > 0 || (p.refactor_lag < 0 && fits));
+    p.max_updates = p.max_updates >= 0 ? p.max_updates : (bg ? 64 : 128);
+    int lag = 0;
+    if (bg) lag = std::min(p.refactor_lag > 0 ? p.refactor_lag : p.max_updates / 2, p.max_updates / 2);
+    ctx->P.max_updates = p.max_updates;
     ctx->P.af_lag = std::max(lag, 0);
     ctx->P.af_reorder = p.refactor_reorder ? 1 : 0;
     ctx->pair = ctx->P.af_lag > 0;
@@ -963,6 +966,7 @@ extern "C" vmc_status vmc_get_stats(vmc_ctx* ctx, int walker, vmc_stats* out) {
   out->async_factor_cycles = h.af_factor_cyc;
   out->factor_set = h.active;
   out->async_lag = ctx->P.af_lag;
+  out->max_updates = ctx->P.max_updates;
   return VMC_OK;
 }
 
@@ -1124,15 +1128,17 @@ extern "C" vmc_status vmc_philox_device(const uint32_t* ctr, const uint32_t* key
 
 // ---- autotuner ---------------------------------------------------------------------
 static vmc_status tune_trial(const vmc_system* systems, int nw, const vmc_solver_params& p, const uint64_t* seeds,
-                             double jitter, double sigma, int steps, void* stream, double* rate, int* lag) {
+                             double jitter, double sigma, int steps, void* stream, double* rate, int* lag, int* mu) {
   vmc_ctx* c = nullptr;
   *rate = 0.0;
   *lag = 0;
+  *mu = p.max_updates;
   vmc_status st = vmc_create(systems, nw, &p, stream, &c);
   if (st == VMC_OK) st = vmc_init_positions(c, seeds, jitter);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (st == VMC_OK) {
     *lag = c->P.af_lag;
+    *mu = c->P.max_updates;
     c->P.step_limit = steps;
     long long moves = 0;
     for (int w = 0; w < nw; ++w) moves += std::min(c->hw[w].n, steps);
@@ -1168,10 +1174,10 @@ extern "C" vmc_status vmc_autotune(const vmc_system* systems, int n_walkers, vmc
     p.max_updates = cd.mu;
     p.refactor_lag = cd.lag;
     double rate = 0.0;
-    int lag = 0;
-    const vmc_status st = tune_trial(systems, n_walkers, p, seeds, jitter, sigma, steps, stream, &rate, &lag);
+    int lag = 0, mu = cd.mu;
+    const vmc_status st = tune_trial(systems, n_walkers, p, seeds, jitter, sigma, steps, stream, &rate, &lag, &mu);
     if (st != VMC_OK && first_err == VMC_OK) first_err = st;
-    vmc_tune_trial t{cd.engine, cd.threads, cd.mu, lag, st == VMC_OK ? rate : 0.0, (int)st};
+    vmc_tune_trial t{cd.engine, cd.threads, mu, lag, st == VMC_OK ? rate : 0.0, (int)st};
     done.push_back(t);
     return st == VMC_OK ? rate : 0.0;
   };
@@ -1182,7 +1188,7 @@ extern "C" vmc_status vmc_autotune(const vmc_system* systems, int n_walkers, vmc
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const bool pairs_fit = 2 * n_walkers <= nsm && mu0 >= 2;  // the rule of refactor_lag = -1
+  const bool pairs_fit = 2 * n_walkers <= nsm && (mu0 < 0 || mu0 >= 2);  // the rule of refactor_lag = -1
   for (int threads : {128, 256}) {
     const Cand cands[3] = {{VMC_ENGINE_PERSISTENT, threads, mu0, -1},
                            {VMC_ENGINE_PERSISTENT, threads, mu0, 0},
@@ -1190,12 +1196,13 @@ extern "C" vmc_status vmc_autotune(const vmc_system* systems, int n_walkers, vmc
     for (const Cand& cd : cands) {
       if (cd.lag == -1 && !pairs_fit) continue;  // would be the same as the next candidate
       const double r = run(cd);
-      if (r > best) { best = r; bc = cd; bc.lag = done.back().refactor_lag; }
+      if (r > best) { best = r; bc = cd; bc.lag = done.back().refactor_lag; bc.mu = done.back().max_updates; }
     }
   }
   // phase 2: chain length for the best mapping
+  const int mu_best = bc.mu;
   for (int mu : {32, 64, 128}) {
-    if (mu == mu0 || mu > kMaxUpd) continue;
+    if (mu == mu_best || mu > kMaxUpd) continue;
     Cand cd = bc;
     cd.mu = mu;
     if (bc.lag > 0) cd.lag = -1;  // background lag follows the chain length (mu / 2)

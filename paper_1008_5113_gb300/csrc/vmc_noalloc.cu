@@ -89,7 +89,8 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   vmc_solver_params p;
   if (params) p = *params;
   else vmc_default_params(&p);
-  if (p.gmres_m < 1 || p.gmres_m > kMaxM || p.max_updates < 0 || p.max_updates > kMaxUpd ||
+  if (p.max_updates < 0) p.max_updates = 128;  // auto: the in-line default
+  if (p.gmres_m < 1 || p.gmres_m > kMaxM || p.max_updates > kMaxUpd ||
       (p.precision != VMC_PREC_FP64 && p.precision != VMC_PREC_MIXED && p.precision != VMC_PREC_MIXED_F32ILU) ||
       (p.block_threads != 0 && (p.block_threads < 64 || p.block_threads > kMaxThreads || p.block_threads % 32)) ||
       !(p.drop_tol >= 0.0) || !(p.permtol >= 0.0) || p.max_restarts < 0)

@@ -60,7 +60,7 @@ class vmc_stats(C.Structure):
                 ("ilu_rows", C.c_int64), ("ilu_elims", C.c_int64), ("ilu_cand", C.c_int64),
                 ("chunks_L", C.c_int), ("chunks_U", C.c_int), ("refactors_async", C.c_int64),
                 ("async_wait_cycles", C.c_int64), ("async_factor_cycles", C.c_int64), ("factor_set", C.c_int),
-                ("async_lag", C.c_int)]
+                ("async_lag", C.c_int), ("max_updates", C.c_int)]
 
 
 class vmc_tune_trial(C.Structure):

@@ -41,6 +41,7 @@ def test_default_params(vmc):
     assert p.drop_tol == 1e-4 and p.permtol == 0.5 and p.gmres_m == 30
     assert p.N_max == 100.0 and p.slow_factor == 4.0 and p.lfil_extra == -1
     assert p.precision == vmc.PREC_MIXED and p.engine == vmc.ENGINE_PERSISTENT
+    assert p.max_updates == -1 and p.refactor_lag == -1 and p.graphs == 1 and p.trisolve == 0
 
 
 @pytest.mark.parametrize("system,why", [
@@ -57,7 +58,7 @@ def test_create_rejects_invalid_systems(vmc, system, why):
     assert e.value.status == 1 and why in str(e.value)
 
 
-@pytest.mark.parametrize("field,value", [("gmres_m", 0), ("gmres_m", 41), ("max_updates", 129),
+@pytest.mark.parametrize("field,value", [("gmres_m", 0), ("gmres_m", 41), ("max_updates", 129), ("max_updates", -2),
                                          ("block_threads", 100), ("block_threads", 1024), ("precision", 3),
                                          ("engine", 7), ("drop_tol", -1.0)])
 def test_create_rejects_invalid_params(vmc, field, value):

@@ -115,11 +115,13 @@ def test_auto_lag(vmc):
     wl = WL.PLAIN_216
     ctx = vmc.vmc_create(wl.systems(), vmc.params())
     try:
-        assert vmc.vmc_get_stats(ctx, 0)["async_lag"] == 32  # max_updates 64 / 2, one walker
+        st = vmc.vmc_get_stats(ctx, 0)  # one walker: pairs fit; chain 64, adopted every 32 accepts
+        assert st["async_lag"] == 32 and st["max_updates"] == 64
     finally:
         vmc.vmc_destroy(ctx)
     ctx = vmc.vmc_create(wl.systems(), vmc.params(engine=vmc.ENGINE_STEP))
     try:
-        assert vmc.vmc_get_stats(ctx, 0)["async_lag"] == 0
+        st = vmc.vmc_get_stats(ctx, 0)  # in-line refactorisation: the longer default chain
+        assert st["async_lag"] == 0 and st["max_updates"] == 128
     finally:
         vmc.vmc_destroy(ctx)
