@@ -341,10 +341,13 @@ def main():
         #      FP32 (mixed mode) ------------------------------------------------------------
         hbm_peak, _ = peaks()
         kr = {}
-        for K, nwk in ((16, 256), (32, 152)):  # n = 4096 with its configuration's 256 walkers
-            ctxk = vmc.vmc_create([(K, 0, A, KAPPA, RC)] * nwk, vmc.params(precision=vmc.PREC_MIXED), stream=stream)
+        # (K, walkers, kappa, r_c): n = 4096 with its configuration's 256 walkers; n = 32768 with
+        # 152 walkers, for the kappa = 2 / r_c = 1.5 matrices and for the large configuration's own
+        # kappa = 1 / r_c = 2 (about 33 entries a row)
+        for K, nwk, kap, rc in ((16, 256, KAPPA, RC), (32, 152, KAPPA, RC), (32, 152, 1.0, 2.0)):
+            ctxk = vmc.vmc_create([(K, 0, A, kap, rc)] * nwk, vmc.params(precision=vmc.PREC_MIXED), stream=stream)
             vmc.vmc_init_positions(ctxk, list(range(1, nwk + 1)), JITTER)
-            reps = 40 if K == 16 else 10
+            reps = 40 if K == 16 else (10 if kap == KAPPA else 4)
             for which, name in ((0, "trisolve"), (1, "spmv")):
                 vmc.vmc_kernel_bench(ctxk, which, 2)
                 vmc.vmc_synchronize(ctxk)
@@ -359,7 +362,8 @@ def main():
                 ms = e0.elapsed_time(e1)
                 by = sum(vmc.vmc_get_stats(ctxk, w)["alg_bytes"] for w in range(nwk))
                 gbs = by / (ms / 1000.0) / 1e9
-                kr[f"{name}_sc{K}_n{K ** 3}_w{nwk}_f32"] = {
+                tag = "" if kap == KAPPA else f"_k{kap:g}_rc{rc:g}"
+                kr[f"{name}_sc{K}_n{K ** 3}{tag}_w{nwk}_f32"] = {
                     "us_per_apply": 1000.0 * ms / reps, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": gbs / hbm_peak, "bytes_per_apply": by / reps}
             vmc.vmc_destroy(ctxk)
