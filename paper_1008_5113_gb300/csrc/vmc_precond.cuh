@@ -178,16 +178,31 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
   T* udinv = reinterpret_cast<T*>(w.u_dinv64);
   int* ulen_a = w.u_len;
   int* levl = w.lev_l;
-  const bool sm_work = (size_t)16 * n <= dbytes;
-  const bool sm_rows = (size_t)32 * n <= dbytes;
+  // Pending L-part labels of the current row: a bitmap over labels (one bit per
+  // label) with a summary word per 32 bitmap words, so that the next label to
+  // eliminate is found with two warp-wide word scans instead of a scan of the row.
+  // They take n/8 bytes and come first, so they stay in shared memory at any n.
+  const int nwords = (n + 31) >> 5;
+  const int nsum = (nwords + 31) >> 5;
+  unsigned* lbits = nullptr;
+  unsigned* lsum = nullptr;
+  const size_t bm_bytes = 4 * (size_t)(pad4(nwords) + pad4(nsum));
+  size_t base = 0;
+  if (bm_bytes <= dbytes) {
+    lbits = (unsigned*)dsm;
+    lsum = lbits + pad4(nwords);
+    base = (bm_bytes + 15) & ~(size_t)15;
+  }
+  const bool sm_work = base + (size_t)16 * n <= dbytes;
+  const bool sm_rows = base + (size_t)32 * n <= dbytes;
   if (sm_work) {
-    wrow = (T*)dsm;
-    wpos = (int*)(dsm + (size_t)8 * n);
+    wrow = (T*)(dsm + base);
+    wpos = (int*)(dsm + base + (size_t)8 * n);
     iperm = wpos + n;
   }
   if (sm_rows) {
-    udinv = (T*)(dsm + (size_t)16 * n);
-    ulen_a = (int*)(dsm + (size_t)24 * n);
+    udinv = (T*)(dsm + base + (size_t)16 * n);
+    ulen_a = (int*)(dsm + base + (size_t)24 * n);
     levl = ulen_a + n;
   }
   // without shared memory the U diagonal lives in the global FP64 array as T values;
@@ -198,20 +213,8 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
   int* ucc = nullptr;
   T* ucv = nullptr;
   int ucap = 0, ufill = 0;
-  // Pending L-part labels of the current row: a bitmap over labels (one bit per
-  // label) with a summary word per 32 bitmap words, so that the next label to
-  // eliminate is found with two warp-wide word scans instead of a scan of the row.
-  const int nwords = (n + 31) >> 5;
-  const int nsum = (nwords + 31) >> 5;
-  unsigned* lbits = nullptr;
-  unsigned* lsum = nullptr;
-  const size_t bm_bytes = 4 * (size_t)(pad4(nwords) + pad4(nsum));
-  if (sm_rows && (size_t)32 * n + bm_bytes <= dbytes) {
-    lbits = (unsigned*)(dsm + (size_t)32 * n);
-    lsum = lbits + pad4(nwords);
-  }
-  const size_t cache_at = (size_t)32 * n + bm_bytes;
-  if (lbits && cache_at + (size_t)4 * n + 16 + 64 * (sizeof(T) + 4) <= dbytes) {
+  const size_t cache_at = base + (size_t)32 * n;
+  if (sm_rows && cache_at + (size_t)4 * n + 16 + 64 * (sizeof(T) + 4) <= dbytes) {
     uoff = (int*)(dsm + cache_at);
     const size_t rest = dbytes - cache_at - (size_t)4 * pad4(n + 1);
     ucap = (int)(rest / (sizeof(T) + 4)) & ~3;
