@@ -113,3 +113,15 @@ def test_autotune_rejects_bad_arguments_without_a_gpu(vmc):
     assert lib.vmc_autotune(sysarr, 1, C.byref(p), seeds, 0.1, 0.2, 0, None, 0, None, None) == 1
     p.engine = vmc.ENGINE_DENSE_SM
     assert lib.vmc_autotune(sysarr, 1, C.byref(p), seeds, 0.1, 0.2, 64, None, 0, None, None) == 1
+
+
+def test_c_example_compiles_against_the_header(tmp_path):
+    """The C example of the ABI compiles as plain C against include/vmc.h."""
+    import shutil
+    import subprocess
+
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    src = os.path.join(ROOT, "paper_1008_5113_gb300", "examples", "vmc_sweep_example.c")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-c", src, "-o",
+                    str(tmp_path / "example.o")], check=True)

@@ -59,3 +59,19 @@ def test_isolated_orbitals_closed_form():
         assert abs(ratio - np.exp(-kappa * d @ d) / A[i, i]) <= 1e-13
         assert np.allclose(grad, -2 * kappa * d, rtol=0, atol=1e-12)
         assert abs(lap - (4 * kappa ** 2 * (d @ d) - 6 * kappa)) <= 1e-11
+
+
+def test_kinetic_energy_equals_minus_half_mean_laplacian_ratio():
+    """Eq. 21 is -(1/2n) sum_p lap_p det A / det A; the oracle's kinetic energy (explicit
+    inverse) and its Laplacian at the unmoved positions (LU solves, ratio 1) must agree."""
+    for sysw, seed in (((4, 0, 1.0, 2.0, 1.5), 3), ((3, 1, 2.031, 1.0, 2.9), 5)):
+        s = O.system(*sysw)
+        Z = O.sites(s)
+        R = O.initial_positions(s, seed, 0.1)
+        n = len(R)
+        lap_sum = 0.0
+        for p in range(n):
+            ratio, _, lap = O.ratio_grad_lap(s, Z, R, p, R[p])
+            assert abs(ratio - 1.0) < 1e-12
+            lap_sum += lap
+        assert abs(O.kinetic_energy(s, Z, R) - (-lap_sum / (2 * n))) <= 1e-10 * max(1.0, abs(lap_sum / n))
