@@ -10,9 +10,10 @@
 //     the reordered matrix A_p = P A Q0 at position r is slot part_of_row[r];
 //   * column labels are "positions": orbital o sits in the fixed column col_of_orb[o]
 //     (orbitals laid out by a 27-colouring of their lattice site, which keeps the
-//     triangular-solve dependency depth small; see vmc_layout.cpp);
+//     triangular-solve dependency depth small; make_layout in vmc_capi.cu);
 //   * ILUTP factors of A_p Q = L U (Sec. 3.2 Eq. 14) in fixed-capacity rows, the
-//     column permutation perm/iperm, and level sets for the triangular solves;
+//     column permutation perm/iperm, level sets and the chunk streams the triangular
+//     solves read (two such factor sets when a second CTA refactors in the background);
 //   * the chain of rank-one preconditioner updates (z_hat_s, u_s) of Sec. 3.2 Eq. 18
 //     with the small matrix G[s][t] = u_s^T z_hat_t;
 //   * the Krylov basis V and preconditioned vectors Zk of GMRES (Sec. 3.2 Eq. 15).
@@ -32,7 +33,6 @@ constexpr int kMaxUpd = 128;      // longest preconditioner update chain
 constexpr int kHistBins = 64;
 constexpr int kSlotBytes = 8192;  // smallest ring slot (a slot holds the largest stream chunk)
 constexpr int kMaxSlots = 8;      // ring depth (chunks in flight)
-constexpr int kChunkRows = 256;   // rows per chunk at most
 constexpr int kChunkHdr = 80;     // chunk header bytes: int4 + 8 next-chunk descriptors
 constexpr int kMaxSeg = 32;       // levels (segments) per chunk at most
 // phase indices of Ctl::cyc

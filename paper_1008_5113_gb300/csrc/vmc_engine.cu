@@ -1,6 +1,10 @@
 // vmc_engine.cu -- kernels of the sparse determinant-ratio engine and their launchers.
 //
-// Every kernel runs one CTA per walker.  A Metropolis step (Sec. 2.2) is:
+// Every kernel runs one CTA per walker, except k_sweep_pair: a cluster of two CTAs per
+// walker, the second refactoring in the background (see the section below).  Besides
+// the sweeps: the single-move calls (k_ratio, with the drift quantities on request;
+// k_accept), the kinetic energy (k_kinetic), set-up and inspection kernels.
+// A Metropolis step (Sec. 2.2) is:
 //   propose r' (Philox, purpose 1) -> Slater row a' and u = a' - a_k (Sec. 3 Eq. 12)
 //   -> solve A_p x = e_r by preconditioned GMRES (Sec. 3.2 Eq. 15) with FP64 refinement
 //   -> controller: reorder + refactor when N > N_max, GMRES fails to converge in m
