@@ -71,7 +71,8 @@ enum { VMC_PREC_FP64 = 0, VMC_PREC_MIXED = 1, VMC_PREC_MIXED_F32ILU = 2 };
 enum {
   VMC_ENGINE_PLAIN = 0,      /* one walker per launch, one launch per move step      */
   VMC_ENGINE_STEP = 1,       /* one launch per move step advancing every walker      */
-  VMC_ENGINE_PERSISTENT = 2, /* one launch per sweep, every walker (CTA per walker)  */
+  VMC_ENGINE_PERSISTENT = 2, /* one launch per sweep, every walker (a CTA per walker,
+                                or a CTA pair with background refactorisation)      */
   VMC_ENGINE_DENSE_SM = 3    /* explicit inverse + Sherman-Morrison (Sec. 1), FP64;
                                 vmc_sweep only (single-move and inspection calls return
                                 VMC_ERR_INVALID); a fresh inverse every sm_refresh sweeps */
@@ -106,8 +107,8 @@ typedef struct {
   int refactor_reorder; /* background refactorisations first re-pair particles and orbitals
                           (the greedy reordering of Sec. 3.1) on the snapshot positions; the
                           solver adopts the new row order with the factors (0) */
-  int trisolve;        /* triangular solves: 0 = level-synchronous (a barrier per level, the
-                          next level's rows gathered ahead of it); 1 = synchronisation-free
+  int trisolve;        /* triangular solves: 0 = level-synchronous (a barrier among the
+                          solving warps per level); 1 = synchronisation-free
                           when both solve vectors fit in shared memory (a warp waits only for
                           the entries its rows read), else level-synchronous (0) */
   int graphs;          /* STEP and PLAIN engines: capture one sweep's launches as a CUDA graph
