@@ -151,3 +151,34 @@ def test_gmres_reference_matches_dense_solve(orc):
         x, its = orc.gmres(rp, ci, cv, e, tol=1e-14)
         assert its > 0
         assert np.abs(x - orc.lu_solve(LU, piv, e)).max() < 1e-12
+
+
+def test_coincident_electrons_make_the_determinant_vanish(orc):
+    """Two electrons at one position give two equal rows of A (Eq. 1), so the determinant is zero:
+    the oracle's LU reports the matrix singular, and moving electron i onto electron j gives the
+    ratio 1 + (a_j - a_i)^T A^{-1} e_i = 1 + delta_ij - 1 = 0 (Eq. 13) from every ratio solver."""
+    s = orc.system(6, 0, 1.0, 2.0, 1.5)
+    Z = orc.sites(s)
+    R = orc.initial_positions(s, 9, 0.1)
+    A = orc.slater_dense(s, Z, R)
+    B = orc.inverse(A)
+    rp, ci, cv = orc.slater_csr(s, Z, R)
+    for i, j in ((3, 4), (100, 7), (215, 214)):
+        a_new = orc.row_dense(s, Z, R[j])
+        assert np.array_equal(a_new, A[j])
+        r, rl = orc.ratio_dense(A, i, a_new)
+        assert abs(r) < 1e-12
+        assert rl == 0.0                      # A' itself is exactly singular
+        assert abs(orc.sm_ratio(B, i, a_new - A[i])) < 1e-12
+        e = np.zeros(A.shape[0]); e[i] = 1.0
+        z, _ = orc.gmres(rp, ci, cv, e, tol=1e-14)
+        assert abs(1.0 + (a_new - A[i]) @ z) < 1e-11
+        R2 = R.copy(); R2[i] = R[j]
+        with pytest.raises(np.linalg.LinAlgError):
+            orc.lu(orc.slater_dense(s, Z, R2))
+    # exactly zero for a small system by the Leibniz sum as well
+    s8 = orc.system(2, 0, 1.0, 0.7, 0.95)
+    Z8 = orc.sites(s8)
+    R8 = orc.initial_positions(s8, 5, 0.15)
+    R8[6] = R8[1]
+    assert abs(orc.leibniz_det(orc.slater_dense(s8, Z8, R8))) < 1e-15
