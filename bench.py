@@ -404,7 +404,7 @@ def main():
                    "refactorizations": sum(s["factorizations"] for s in stats)},
     }
     out.update(extra)
-    if not args.no_cpu_baseline and world >= 1:
+    if not args.no_cpu_baseline and world == 1:  # timed on the host cores at N = 1 only
         try:
             out["cpu_baseline"] = cpu_oracle_sample(6)[0]  # about 10 s on the host cores
         except Exception as e:  # the oracle is test infrastructure; report, do not fail
