@@ -204,7 +204,6 @@ def main():
         return reference_arm(args)
     args.warmup = max(3, args.warmup)
 
-    import numpy as np
     import torch
 
     from paper_1008_5113_gb300 import vmc
@@ -288,9 +287,15 @@ def main():
     for _ in range(args.warmup):
         vmc.vmc_sweep_async(ctx, 1, SIGMA, seeds_dev)
     vmc.vmc_synchronize(ctx)
-    host_seeds = np.array(seeds, dtype=np.uint64)
-    acc_log = np.zeros(WALKERS * N, dtype=np.uint8)
-    rat_log = np.zeros(WALKERS * N)
+    # the step's inputs and results live in pinned host memory (pageable if pinning fails)
+    host_seeds = torch.tensor(seeds, dtype=torch.int64)        # the seeds' uint64 bytes (all positive)
+    acc_log = torch.zeros(WALKERS * N, dtype=torch.uint8)
+    rat_log = torch.zeros(WALKERS * N, dtype=torch.float64)
+    try:
+        host_seeds, acc_log, rat_log = host_seeds.pin_memory(), acc_log.pin_memory(), rat_log.pin_memory()
+        host_memory = "pinned"
+    except RuntimeError:
+        host_memory = "pageable"
     lib = vmc.lib()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -392,8 +397,11 @@ def main():
                    "l2": "256 MB buffer written between timed steps"},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * WALKERS,
-                "d2h_bytes_per_step": 9 * WALKERS * N},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": host_seeds.numel() * host_seeds.element_size(),
+                "d2h_bytes_per_step": acc_log.numel() * acc_log.element_size()
+                + rat_log.numel() * rat_log.element_size(),
+                "host_memory": host_memory, "api": "vmc_sweep (host seeds in, accept and ratio logs out)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": profiled_traffic(f"{kernel_name}_sc10_n1000_w64_fp64.md"),
                      "note": f"{kernel_name}, algorithmic bytes from the kernel's per-phase counter; peak "
