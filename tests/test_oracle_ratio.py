@@ -182,3 +182,22 @@ def test_coincident_electrons_make_the_determinant_vanish(orc):
     R8 = orc.initial_positions(s8, 5, 0.15)
     R8[6] = R8[1]
     assert abs(orc.leibniz_det(orc.slater_dense(s8, Z8, R8))) < 1e-15
+
+
+@pytest.mark.parametrize("kappa,r_c", [(2.0, 1.5), (1.0, 2.0)])
+def test_gmres_reference_at_n_1728(orc, kappa, r_c):
+    """The restarted GMRES that the oracle uses above n = 1000 (Sec. 3.2; x0 = 0, so the
+    relative residual is the absolute one) against dense LU at n = 12^3, for both orbital
+    widths of the configured workloads; the residual is recomputed here with numpy."""
+    s = orc.system(12, 0, 1.0, kappa, r_c)
+    Z = orc.sites(s)
+    R = orc.initial_positions(s, 3, 0.1)
+    A = orc.slater_dense(s, Z, R)
+    rp, ci, cv = orc.slater_csr(s, Z, R)
+    LU, piv, _ = orc.lu(A)
+    for i in (0, 777, 1727):
+        e = np.zeros(A.shape[0]); e[i] = 1.0
+        x, its = orc.gmres(rp, ci, cv, e, tol=1e-14)
+        assert its > 0
+        assert np.linalg.norm(A @ x - e) <= 1e-13
+        assert np.abs(x - orc.lu_solve(LU, piv, e)).max() <= 1e-12
