@@ -47,8 +47,35 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def strip_c_comments(text: str) -> str:
+    """C/C++/CUDA source without its comments, trailing blanks and empty lines (string and
+    character literals are kept as written)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = ("".join(out)).split("\n")
+    return "\n".join(ln.rstrip() for ln in lines if ln.strip())
+
+
 def sources_digest() -> str:
-    """SHA-256 over the CUDA sources and the C header (identifies the kernels' build)."""
+    """SHA-256 over the CUDA sources and the C header with their comments removed: it
+    identifies the code the kernels are built from, and comment edits leave it alone."""
     import hashlib
 
     h = hashlib.sha256()
@@ -57,7 +84,7 @@ def sources_digest() -> str:
         path = os.path.normpath(os.path.join(csrc, f))
         if os.path.isfile(path):
             h.update(f.encode())
-            h.update(open(path, "rb").read())
+            h.update(strip_c_comments(open(path, encoding="utf-8").read()).encode())
     return h.hexdigest()
 
 

@@ -55,3 +55,17 @@ def test_profiled_traffic_requires_matching_sources(tmp_path, monkeypatch):
     assert bench.profiled_traffic("k_good.md") == 1234.0
     assert bench.profiled_traffic("k_stale.md") is None
     assert bench.profiled_traffic("k_missing.md") is None
+
+
+def test_source_digest_ignores_comments_only():
+    import bench
+
+    code = 'int f(int x) {\n  return x + 1;  // one\n}\nconst char* s = "// kept /* too */";\n'
+    commented = '/* header\n   text */\nint f(int x) {\n\n  return x + 1;  // two, longer\n}\n' \
+                'const char* s = "// kept /* too */";  /* trailing */\n'
+    changed = code.replace("x + 1", "x + 2")
+    strip = bench.strip_c_comments
+    assert strip(code) == strip(commented)
+    assert strip(code) != strip(changed)
+    assert '"// kept /* too */"' in strip(code)
+    assert strip("char c = '\\''; // q\nint y;") == "char c = '\\'';\nint y;"
