@@ -156,7 +156,7 @@ typedef struct {
   int max_updates;           /* the max_updates in effect                                   */
 } vmc_stats;
 
-/* Fill p with the defaults above. */
+/* Fill p (host) with the defaults above; VMC_ERR_INVALID for NULL. */
 vmc_status vmc_default_params(vmc_solver_params* p);
 
 /* One autotuner trial (see vmc_autotune). */
@@ -187,28 +187,47 @@ vmc_status vmc_autotune(const vmc_system* systems, int n_walkers, vmc_solver_par
                         int* n_trials, void* stream);
 
 /* Create a context for n_walkers walkers; systems[w] is walker w's system
- * (walkers may differ in size: an uneven batch).  stream: a cudaStream_t (or NULL
- * for the default stream) on which every device operation of the context runs.
+ * (walkers may differ in size: an uneven batch).  systems: host, n_walkers entries,
+ * copied.  params: host, copied; NULL means the defaults.  stream: a cudaStream_t (or
+ * NULL for the default stream) on which every device operation of the context runs.
  * Allocates all device memory up front.  Positions must be set next
- * (vmc_init_positions or vmc_set_positions). */
+ * (vmc_init_positions or vmc_set_positions).
+ * Errors: VMC_ERR_INVALID for a NULL out or systems or n_walkers outside [1, 65535]
+ * (then *out is NULL), and for a parameter or a system out of range (the message names
+ * it); VMC_ERR_OOM / VMC_ERR_CUDA when device allocation or set-up fails or no usable
+ * device is current.  In every case but the first *out still receives the context so
+ * that vmc_last_error can describe the failure: release it with vmc_destroy. */
 vmc_status vmc_create(const vmc_system* systems, int n_walkers, const vmc_solver_params* params,
                       void* stream, vmc_ctx** out);
+/* Free every device allocation of the context and the context itself (device work
+ * still queued on its stream completes first).  VMC_ERR_INVALID for NULL. */
 vmc_status vmc_destroy(vmc_ctx* ctx);
 
 /* Start walker w at r_i = wrap(Z_i + jitter N(0,1)^3) with normals from
  * Philox4x32-10(key = seeds[w], counter = (0, i, 0, j)), for every walker; then build
  * the Slater matrices, reorder (Sec. 3.1) and factor (Sec. 3.2).  seeds: host,
- * n_walkers entries. */
+ * n_walkers entries.  Resets every walker's statistics and status and drops pending
+ * ratios.  Errors: VMC_ERR_INVALID (NULL seeds, negative or NaN jitter), VMC_ERR_CUDA,
+ * or the first failing walker's status (e.g. VMC_ERR_CAPACITY). */
 vmc_status vmc_init_positions(vmc_ctx* ctx, const uint64_t* seeds, double jitter);
-/* Set walker w's positions (host, n*3 doubles, particle order) and rebuild its matrix,
- * ordering and factorisation. */
+/* Set walker w's positions (host, n*3 doubles, particle order; wrapped into the box)
+ * and rebuild its matrix, ordering and factorisation; resets that walker's statistics
+ * and status.  Errors: VMC_ERR_INVALID (NULL xyz, walker out of range, a non-finite
+ * coordinate), VMC_ERR_CUDA, or the walker's failure status. */
 vmc_status vmc_set_positions(vmc_ctx* ctx, int walker, const double* xyz);
+/* Copy walker w's current positions (particle order, in [0, L)) to xyz (host, n*3
+ * doubles); synchronises the stream.  VMC_ERR_INVALID for bad arguments. */
 vmc_status vmc_get_positions(vmc_ctx* ctx, int walker, double* xyz);
+/* Walker w's particle count n (K^3 or 2K^3), or -1 for bad arguments. */
 int vmc_walker_n(const vmc_ctx* ctx, int walker);
 
 /* Single move: det(A')/det(A) for moving particle k of walker w to r_new (host, 3
  * doubles; wrapped into the box).  Nothing is committed; the solve is kept so that
- * vmc_accept can commit it.  Sec. 3 Eq. 13. */
+ * vmc_accept can commit it.  Sec. 3 Eq. 13.  ratio: host, written on success.
+ * Errors: VMC_ERR_INVALID (dense engine, NULL pointers, walker or k out of range, a
+ * non-finite coordinate), VMC_ERR_STATE (positions not set), VMC_ERR_NOCONV (the solve
+ * did not converge after reorder + restarts; nothing is pending), or the walker's
+ * failure status. */
 vmc_status vmc_ratio(vmc_ctx* ctx, int walker, int k, const double r_new[3], double* ratio);
 /* vmc_ratio plus the quantities of a drift-diffusion step at the proposed position
  * (Sec. 2.2; the same solve: column k of A'^{-1} is A^{-1} e_k / ratio):
@@ -227,12 +246,20 @@ vmc_status vmc_accept(vmc_ctx* ctx, int walker);
 /* Metropolis sweeps (Sec. 2.2): every walker moves particles 0..n-1 in order,
  * r' = wrap(r + sigma N(0,1)^3) (counter (sweep, i, 1, j)), accepted iff
  * ratio^2 > U with U from counter (sweep, i, 2, 0), key seeds[w].  Sweep indices
- * continue from the context's sweep counter.  Logs (host, nullable): walker-major,
- * sum_w n_sweeps * n_w entries, walker w's block starting at n_sweeps * (n_0 + ... + n_{w-1}). */
+ * continue from the context's sweep counter.  seeds: host, n_walkers entries.  Logs
+ * (host, nullable): walker-major, sum_w n_sweeps * n_w entries, walker w's block starting
+ * at n_sweeps * (n_0 + ... + n_{w-1}); the device buffers behind them are grown as needed
+ * and owned by the context.  Pending ratios are dropped.  Returns after the logs are
+ * written.  Errors: VMC_ERR_INVALID (NULL seeds, n_sweeps < 0, negative or NaN sigma),
+ * VMC_ERR_STATE (positions not set), VMC_ERR_OOM (log buffers), VMC_ERR_CUDA, or the
+ * first failing walker's status. */
 vmc_status vmc_sweep(vmc_ctx* ctx, int n_sweeps, double sigma, const uint64_t* seeds,
                      uint8_t* accept_log, double* ratio_log);
 /* Same, with device-resident logs (nullable) and no host synchronisation: the call
- * only enqueues work on the context's stream. */
+ * only enqueues work on the context's stream.  seeds_dev and the logs (device, owned by
+ * the caller) must stay valid until that work completes; walker failures surface at
+ * vmc_synchronize.  Errors at enqueue: VMC_ERR_INVALID, VMC_ERR_STATE, VMC_ERR_OOM (the
+ * sweep graph's state), VMC_ERR_CUDA. */
 vmc_status vmc_sweep_async(vmc_ctx* ctx, int n_sweeps, double sigma, const uint64_t* seeds_dev,
                            uint8_t* accept_log_dev, double* ratio_log_dev);
 /* Device status check after vmc_sweep_async: synchronises and returns the first
@@ -249,11 +276,20 @@ vmc_status vmc_synchronize(vmc_ctx* ctx);
  * VMC_ERR_STATE before positions are set. */
 vmc_status vmc_kinetic_energy(vmc_ctx* ctx, double* energy);
 
+/* Walker w's statistics (host struct, written before return; synchronises the stream).
+ * VMC_ERR_INVALID for bad arguments. */
 vmc_status vmc_get_stats(vmc_ctx* ctx, int walker, vmc_stats* out);
+/* Zero every walker's event counters (proposals, accepts, solves, iterations, reorders,
+ * refactorisations), the monitor's max and sum, the histogram, the cycle counts and the
+ * algorithmic bytes; the status and the description of the current state (nonzeros,
+ * level counts, chain length, factor set) are kept.  Synchronises the stream. */
 vmc_status vmc_reset_stats(vmc_ctx* ctx);
+/* Text of the most recent failure on ctx (owned by ctx, valid until its next call);
+ * "null context" for NULL. */
 const char* vmc_last_error(const vmc_ctx* ctx);
-/* Sweeps done so far (the sweep counter used for the proposals). */
+/* Sweeps done so far (the sweep counter used for the proposals); -1 for NULL. */
 int64_t vmc_sweep_count(const vmc_ctx* ctx);
+/* Set the sweep counter (to replay a stretch of a chain); VMC_ERR_INVALID if negative. */
 vmc_status vmc_set_sweep_count(vmc_ctx* ctx, int64_t sweeps);
 
 /* ---- inspection (tests) -------------------------------------------------------- */
