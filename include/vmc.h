@@ -103,7 +103,9 @@ typedef struct {
                           Eqs. 16-18 hold for any root), so results do not depend on timing.
                           0: off (refactor in line when the chain is full); > 0: on, clamped
                           to max_updates / 2; -1: auto -- on with max_updates / 2 when every
-                          walker pair fits on the GPU at once (2 x walkers <= SMs) (-1) */
+                          walker pair fits on the GPU at once (2 x walkers <= SMs) and no
+                          system exceeds n = 8192 (beyond that one factorisation outlasts
+                          the accepts between adoptions and in-line refactoring is faster) (-1) */
   int refactor_reorder; /* background refactorisations first re-pair particles and orbitals
                           (the greedy reordering of Sec. 3.1) on the snapshot positions; the
                           solver adopts the new row order with the factors (0) */

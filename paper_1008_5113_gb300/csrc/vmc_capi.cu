@@ -176,6 +176,21 @@ static vmc_status cuda_fail(vmc_ctx* c, cudaError_t e, const char* what) {
 
 static LaunchCfg cfg(const vmc_ctx* c) { return LaunchCfg{c->stream, c->threads, c->fp64, c->smem}; }
 
+// Automatic background refactorisation (refactor_lag = -1) needs every walker pair on
+// the GPU at once, and systems small enough that a factorisation by one warp finishes
+// within the accepts between adoptions: at n = 1000 it takes a fraction of them, at
+// n = 32768 (about 28 s) many times more, and in-line refactoring is faster there.
+constexpr long long kAutoPairMaxN = 8192;
+
+static bool auto_pairs_fit(const vmc_system* systems, int n_walkers, int nsm) {
+  if (nsm <= 0 || 2 * n_walkers > nsm) return false;
+  for (int w = 0; w < n_walkers; ++w) {
+    const long long K = std::min(std::max(systems[w].K, 0), 1 << 10);
+    if (K * K * K * (systems[w].lattice == 1 ? 2 : 1) > kAutoPairMaxN) return false;
+  }
+  return true;
+}
+
 extern "C" vmc_status vmc_default_params(vmc_solver_params* p) {
   if (!p) return VMC_ERR_INVALID;
   p->drop_tol = 1e-4;
@@ -329,12 +344,13 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   ctx->P.slow_factor = p.slow_factor;
   {
     // background refactorisation (persistent engine) when asked for, or by default when
-    // every walker pair fits; the chain length defaults to 64 with it (adopted every 32
-    // accepts) and to 128 without (in-line refactorisations are the costlier)
+    // every walker pair fits and no system is larger than kAutoPairMaxN; the chain length
+    // defaults to 64 with it (adopted every 32 accepts) and to 128 without (in-line
+    // refactorisations are the costlier)
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const bool fits = nsm > 0 && 2 * n_walkers <= nsm;
+    const bool fits = auto_pairs_fit(systems, n_walkers, nsm);
     const bool bg = p.engine == VMC_ENGINE_PERSISTENT && (p.refactor_lag > 0 || (p.refactor_lag < 0 && fits));
     p.max_updates = p.max_updates >= 0 ? p.max_updates : (bg ? 64 : 128);
     int lag = 0;
@@ -1188,7 +1204,7 @@ extern "C" vmc_status vmc_autotune(const vmc_system* systems, int n_walkers, vmc
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const bool pairs_fit = 2 * n_walkers <= nsm && (mu0 < 0 || mu0 >= 2);  // the rule of refactor_lag = -1
+  const bool pairs_fit = auto_pairs_fit(systems, n_walkers, nsm) && (mu0 < 0 || mu0 >= 2);  // refactor_lag = -1's rule
   for (int threads : {128, 256}) {
     const Cand cands[3] = {{VMC_ENGINE_PERSISTENT, threads, mu0, -1},
                            {VMC_ENGINE_PERSISTENT, threads, mu0, 0},
