@@ -105,7 +105,9 @@ typedef struct {
                           to max_updates / 2; -1: auto -- on with max_updates / 2 when every
                           walker pair fits on the GPU at once (2 x walkers <= SMs) and no
                           system exceeds n = 8192 (beyond that one factorisation outlasts
-                          the accepts between adoptions and in-line refactoring is faster) (-1) */
+                          the accepts between adoptions and in-line refactoring is faster;
+                          at n = 32768 it takes about 28 s, near the 30 s bound on the
+                          solver's wait, past which the walker reports VMC_ERR_TIMEOUT) (-1) */
   int refactor_reorder; /* background refactorisations first re-pair particles and orbitals
                           (the greedy reordering of Sec. 3.1) on the snapshot positions; the
                           solver adopts the new row order with the factors (0) */
