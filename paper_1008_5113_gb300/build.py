@@ -1,6 +1,7 @@
 """In-tree build of the CUDA library ``libvmc.so`` for sm_103a (nvcc, no cmake).
 
-The two translation units (kernels; C ABI + host layout) compile in parallel and are
+The four translation units (engine kernels; C ABI + host layout; the allocation-free
+entry point; the dense reference engine) compile in parallel and are
 linked into ``paper_1008_5113_gb300/libvmc.so`` next to this file.
 """
 from __future__ import annotations
