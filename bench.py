@@ -168,15 +168,16 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_oracle_sample(sweeps: int = 1):
+def cpu_oracle_sample(sweeps: int = 1, threads: int = 0):
     """Time the FP64 oracle (explicit inverse + Sherman-Morrison chain) on the host cores:
-    one walker per core, `sweeps` sweeps of n moves each.  Returns (record, ratios, seconds)."""
+    one walker per thread (all cores when threads = 0), `sweeps` sweeps of n moves each.
+    Returns (record, ratios, seconds)."""
     import numpy as np
 
     import oracle
 
     oracle.build()
-    threads = oracle.max_threads()
+    threads = threads if threads > 0 else len(os.sched_getaffinity(0))  # every core this process may use
     s = oracle.system(K_LAT, 0, A, KAPPA, RC)
     nw = max(1, threads)
     seeds = list(range(1, nw + 1))
@@ -442,6 +443,7 @@ def main():
     if not args.no_cpu_baseline and world == 1:  # timed on the host cores at N = 1 only
         try:
             out["cpu_baseline"] = cpu_oracle_sample(6)[0]  # about 10 s on the host cores
+            out["cpu_baseline_1core"] = cpu_oracle_sample(2, threads=1)[0]
         except Exception as e:  # the oracle is test infrastructure; report, do not fail
             out["cpu_baseline"] = {"value": None, "error": str(e)}
     print(json.dumps(out), flush=True)
