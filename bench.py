@@ -3,16 +3,29 @@
 Workload: n = 1000 electrons/orbitals on a 10x10x10 simple-cubic lattice (a = 1),
 Gaussian orbitals exp(-2 |r - Z|^2) cut at r_c = 1.5, 64 independent walkers
 (seeds 1..64), electrons started at the sites + N(0, 0.1^2), Metropolis steps
-N(0, 0.2^2), FP64 arithmetic ("plain FP64 batched").  One bench step = one sweep
-of every walker: 64 x 1000 determinant ratios through the whole hot path
-(proposal, Slater row, ILUTP-preconditioned GMRES solve with refinement,
-stability monitor/reorder/refactor, Metropolis test, row commit and
-preconditioner update).  Synthetic data, nothing read from disk.
+N(0, 0.2^2), FP64 arithmetic ("plain FP64 batched").  Synthetic data, nothing read
+from disk.
 
-Reported beside the headline: the same workload in mixed precision, the plain
-FP64 one-walker-per-launch path (the metric's denominator), the roofline of the
-dominant kernel from its algorithmic-byte counter, and the FP64 CPU oracle timed
-on the host cores.
+Stationary timed step.  The first sweeps of a chain are a transient: the electrons
+leave their start positions and the Slater matrices grow harder to solve (the paper
+discards 20 sweeps, Sec. 4).  So the walkers are first taken through S = 20 sweeps
+by the engine's dense Sherman-Morrison path (FP64, untimed; the same Markov chain);
+their positions and the sweep counter S are the saved state.  Every bench step --
+warm-up and timed -- restores that state (vmc_set_positions_all: rows, reordering and
+a fresh ILUTP per walker; vmc_set_sweep_count(S)), outside the timed region, and then
+times the first 250 moves of sweep S of every walker (particles 0..249, a quarter
+sweep): 64 x 250 determinant ratios through the whole hot path (proposal, Slater row,
+ILUTP-preconditioned GMRES solve with refinement, stability monitor/reorder/refactor,
+Metropolis test, row commit and preconditioner update, background refactorisations).
+Every step is the same piece of work.
+
+Reported beside the headline: the end-to-end rate through the host API, the same
+sweep in mixed precision, the dense Sherman-Morrison reference point, the plain FP64
+one-walker-per-launch path (the metric's denominator) on walker 0's sweep S, the
+roofline of the dominant kernel from its algorithmic-byte counter, per-kernel
+rooflines of the triangular solves and the SpMV at the HBM-sized configurations, and
+the FP64 CPU oracle timed on the host cores.  Legs after the headline are skipped
+once the wall-clock budget (--budget-s) is spent; each leg's wall time goes to stderr.
 
 Multi-GPU (torchrun): every rank runs its own 64 walkers (weak scaling, replicas:
 walkers are independent Markov chains, nothing is exchanged on the data path);
@@ -40,6 +53,8 @@ METRIC = "det-ratio evals/sec over walker batch vs plain FP64 path; % of HBM roo
 UNIT = "det-ratio evals/s"
 K_LAT, KAPPA, RC, A, JITTER, SIGMA, WALKERS = 10, 2.0, 1.5, 1.0, 0.1, 0.2, 64
 N = K_LAT ** 3
+EQUIL_SWEEPS = 20  # sweeps discarded before the timed sweep (Sec. 4 discards 20)
+MOVES_PER_STEP = 250  # moves per walker in one bench step (particles 0..249 of sweep S)
 WORKLOAD = "sc10_n1000_kappa2_rc1.5_w64_fp64"
 
 
@@ -218,20 +233,35 @@ def reference_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def log(msg: str) -> None:
+    print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--budget-s", type=float, default=900.0,
+                    help="wall-clock budget: legs after the headline are skipped once it is spent")
+    ap.add_argument("--walkers", type=int, default=WALKERS, help="walkers per GPU (profiling runs use fewer)")
+    ap.add_argument("--moves", type=int, default=MOVES_PER_STEP,
+                    help="moves per walker in a step: the first moves of sweep S (0: the full sweep)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-kernels", action="store_true")
+    ap.add_argument("--headline-only", action="store_true", help="skip every leg after the headline")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
     args.warmup = max(3, args.warmup)
+    t_start = time.perf_counter()
 
+    def over_budget() -> bool:
+        return time.perf_counter() - t_start > args.budget_s
+
+    import numpy as np
     import torch
 
     from paper_1008_5113_gb300 import vmc
@@ -253,136 +283,160 @@ def main():
     stream = torch.cuda.current_stream()
     from paper_1008_5113_gb300 import replicas
 
-    systems = [(K_LAT, 0, A, KAPPA, RC)] * WALKERS
-    seeds = replicas.walker_seeds(rank, WALKERS)
-
-    def make(prec, engine, nw=WALKERS):
-        ctx = vmc.vmc_create(systems[:nw], vmc.params(precision=prec, engine=engine), stream=stream)
-        vmc.vmc_init_positions(ctx, seeds[:nw], JITTER)
-        return ctx
-
-    def refactor_mode(ctx):
-        lag = vmc.vmc_get_stats(ctx, 0)["async_lag"]
-        if lag > 0:
-            return (f"background: a factor CTA per walker (cluster of 2) refactors a snapshot, adopted "
-                    f"{lag} accepts later")
-        return "in line, when the update chain is full"
-
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    NW = args.walkers
+    moves = args.moves if 0 < args.moves < N else N
+    systems = [(K_LAT, 0, A, KAPPA, RC)] * NW
+    seeds = replicas.walker_seeds(rank, NW)
     seeds_dev = torch.tensor(seeds, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def timed_sweeps(ctx, steps, warmup, keep_state=None):
-        for _ in range(warmup):
-            vmc.vmc_sweep_async(ctx, 1, SIGMA, seeds_dev)
-        vmc.vmc_synchronize(ctx)
-        if keep_state is not None:  # walker 0 where the timed sweeps start (for the plain path)
-            keep_state["R0"] = vmc.vmc_get_positions(ctx, 0)
-            keep_state["sweep"] = vmc.vmc_sweep_count(ctx)
-        vmc.vmc_reset_stats(ctx)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k in range(steps):
+    # ---- the saved state: S sweeps of the dense Sherman-Morrison engine (untimed) --------
+    t0 = time.perf_counter()
+    ctxd = vmc.vmc_create(systems, vmc.params(precision=vmc.PREC_FP64, engine=vmc.ENGINE_DENSE_SM), stream=stream)
+    vmc.vmc_init_positions(ctxd, seeds, JITTER)
+    vmc.vmc_sweep_async(ctxd, EQUIL_SWEEPS, SIGMA, seeds_dev)
+    vmc.vmc_synchronize(ctxd)
+    state = np.concatenate([vmc.vmc_get_positions(ctxd, w).reshape(-1) for w in range(NW)])
+    vmc.vmc_destroy(ctxd)
+    log(f"equilibration: {EQUIL_SWEEPS} dense sweeps of {NW} walkers in {time.perf_counter() - t0:.1f} s")
+
+    def make(prec, engine, nw=NW):
+        return vmc.vmc_create(systems[:nw], vmc.params(precision=prec, engine=engine, sweep_moves=args.moves),
+                              stream=stream)
+
+    def restore(ctx, nw=NW):
+        vmc.vmc_set_positions_all(ctx, state[:nw * N * 3])
+        vmc.vmc_set_sweep_count(ctx, EQUIL_SWEEPS)
+
+    def stationary_sweeps(ctx, steps, warmup, nw=NW):
+        """warmup + steps times: restore (untimed), flush L2, time sweep S on the stream.
+        Returns per-step ms and the statistics summed over the timed steps."""
+        ms, acc = [], None
+        for k in range(warmup + steps):
+            restore(ctx, nw)
             flush.fill_(float(k))                      # L2 flush between timed steps (not timed)
-            ev[k][0].record(stream)
-            vmc.vmc_sweep_async(ctx, 1, SIGMA, seeds_dev)
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        vmc.vmc_synchronize(ctx)
-        ms = [a.elapsed_time(b) for a, b in ev]
-        return sum(ms), ms, wall
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if world > 1 and k == warmup:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            vmc.vmc_sweep_async(ctx, 1, SIGMA, seeds_dev[:nw])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            vmc.vmc_synchronize(ctx)
+            if k >= warmup:
+                ms.append(e0.elapsed_time(e1))
+                st = [vmc.vmc_get_stats(ctx, w) for w in range(nw)]
+                if acc is None:
+                    acc = st
+                else:
+                    for a, b in zip(acc, st):
+                        for key, v in b.items():
+                            if isinstance(v, list):
+                                a[key] = [x + y for x, y in zip(a[key], v)]
+                            elif key not in ("status", "factor_set", "async_lag", "max_updates", "n_updates",
+                                             "levels_L", "levels_U", "nnz_A", "nnz_LU", "pivots", "chunks_L",
+                                             "chunks_U", "N_max_seen"):
+                                a[key] += v
+                            elif key == "N_max_seen":
+                                a[key] = max(a[key], v)
+        return ms, acc
 
-    # ---- headline: batched FP64, persistent engine (one launch per sweep) ------------
+    # ---- headline: batched FP64, persistent engine (one launch per sweep) ---------------
+    t0 = time.perf_counter()
     ctx = make(vmc.PREC_FP64, vmc.ENGINE_PERSISTENT)
-    refactoring = refactor_mode(ctx)
-    state = {}
-    kernel_name = "k_sweep_pair" if vmc.vmc_get_stats(ctx, 0)["async_lag"] > 0 else "k_sweep"
+    lag = vmc.vmc_get_stats(ctx, 0)["async_lag"]
+    refactoring = (f"background: a factor CTA per walker (cluster of 2) refactors a snapshot, adopted {lag} "
+                   f"accepts later" if lag > 0 else "in line, when the update chain is full")
+    kernel_name = "k_sweep_pair" if lag > 0 else "k_sweep"
     with Clocks(dev) as clk:
-        total_ms, per_ms, wall = timed_sweeps(ctx, args.steps, args.warmup, keep_state=state)
-    stats = [vmc.vmc_get_stats(ctx, w) for w in range(WALKERS)]
+        per_ms, stats = stationary_sweeps(ctx, args.steps, args.warmup)
+    total_ms = sum(per_ms)
     ratios_local = sum(s["proposals"] for s in stats)
-    assert ratios_local == args.steps * WALKERS * N, (ratios_local, args.steps)
+    assert ratios_local == args.steps * NW * moves, (ratios_local, args.steps)
     ratios_all, t_max = replicas.reduce_run(ratios_local, total_ms)
     value = replicas.throughput(ratios_all, t_max / 1000.0)
     alg_bytes = sum(s["alg_bytes"] for s in stats)
-    vmc.vmc_destroy(ctx)
-    # ---- e2e: public host API, host seeds in, host logs out, every step; a fresh context
-    #      brought to the same state, so the timed sweeps are the same sweeps as above -----
-    ctx = make(vmc.PREC_FP64, vmc.ENGINE_PERSISTENT)
-    for _ in range(args.warmup):
-        vmc.vmc_sweep_async(ctx, 1, SIGMA, seeds_dev)
-    vmc.vmc_synchronize(ctx)
-    # the step's inputs and results live in pinned host memory (pageable if pinning fails)
+    log(f"headline: {args.warmup}+{args.steps} sweeps in {time.perf_counter() - t0:.1f} s; "
+        f"{value:.0f} ratios/s; per step ms {[round(x) for x in per_ms]}")
+    # ---- e2e: public host API (host seeds in, accept and ratio logs out, every step), the
+    #      same restored sweeps on the same context -----------------------------------------
+    t0 = time.perf_counter()
     host_seeds = torch.tensor(seeds, dtype=torch.int64)        # the seeds' uint64 bytes (all positive)
-    acc_log = torch.zeros(WALKERS * N, dtype=torch.uint8)
-    rat_log = torch.zeros(WALKERS * N, dtype=torch.float64)
+    acc_log = torch.zeros(NW * N, dtype=torch.uint8)
+    rat_log = torch.zeros(NW * N, dtype=torch.float64)
     try:
         host_seeds, acc_log, rat_log = host_seeds.pin_memory(), acc_log.pin_memory(), rat_log.pin_memory()
         host_memory = "pinned"
     except RuntimeError:
         host_memory = "pageable"
     lib = vmc.lib()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        st = lib.vmc_sweep(ctx, 1, SIGMA, vmc._p(host_seeds), vmc._p(acc_log), vmc._p(rat_log))
-        assert st == 0, vmc.vmc_last_error(ctx)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_count, e2e_s = replicas.reduce_run(args.steps * WALKERS * N, e2e_s)
+    e2e_s = 0.0
+    for k in range(args.steps + 1):   # the first call sizes the context's log buffers: untimed
+        restore(ctx)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        st_ = lib.vmc_sweep(ctx, 1, SIGMA, vmc._p(host_seeds), vmc._p(acc_log), vmc._p(rat_log))
+        if k > 0:
+            e2e_s += time.perf_counter() - t1
+        assert st_ == 0, vmc.vmc_last_error(ctx)
+    e2e_count, e2e_s = replicas.reduce_run(args.steps * NW * moves, e2e_s)
     e2e_value = replicas.throughput(e2e_count, e2e_s)
     vmc.vmc_destroy(ctx)
+    log(f"e2e: {args.steps} sweeps in {time.perf_counter() - t0:.1f} s; {e2e_value:.0f} ratios/s")
 
-    extra = {}
-    if rank == 0:
-        # ---- mixed precision, same workload ----------------------------------------------
-        ctxm = make(vmc.PREC_MIXED, vmc.ENGINE_PERSISTENT)
-        tm, _, _ = timed_sweeps(ctxm, args.steps, args.warmup)
-        sm = [vmc.vmc_get_stats(ctxm, w) for w in range(WALKERS)]
-        extra["mixed_value"] = sum(s["proposals"] for s in sm) / (tm / 1000.0)
-        vmc.vmc_destroy(ctxm)
+    extra, skipped = {}, []
+    side_steps = max(1, min(args.steps, 3))   # fixed-size side legs: at most 3 timed + 1 warm-up
+    if rank == 0 and not args.headline_only:
+        # ---- mixed precision, same restored sweep ----------------------------------------
+        if not over_budget():
+            t0 = time.perf_counter()
+            ctxm = make(vmc.PREC_MIXED, vmc.ENGINE_PERSISTENT)
+            ms_m, sm = stationary_sweeps(ctxm, side_steps, 1)
+            extra["mixed_value"] = sum(s["proposals"] for s in sm) / (sum(ms_m) / 1000.0)
+            extra["mixed_inner_its_per_ratio"] = sum(s["inner_iterations"] for s in sm) / sum(s["proposals"] for s in sm)
+            vmc.vmc_destroy(ctxm)
+            log(f"mixed: {time.perf_counter() - t0:.1f} s; {extra['mixed_value']:.0f} ratios/s")
+        else:
+            skipped.append("mixed")
         # ---- the dense reference point: explicit inverse + Sherman-Morrison (Sec. 1), FP64,
-        #      same walkers and sweeps, a fresh inverse every sweep -------------------------
-        ctxd = make(vmc.PREC_FP64, vmc.ENGINE_DENSE_SM)
-        td, _, _ = timed_sweeps(ctxd, args.steps, args.warmup)
-        sd_ = [vmc.vmc_get_stats(ctxd, w) for w in range(WALKERS)]
-        extra["dense_sm_fp64_value"] = sum(x["proposals"] for x in sd_) / (td / 1000.0)
-        vmc.vmc_destroy(ctxd)
-        # ---- plain FP64 one-walker-per-launch path (bounded sample: 1 walker, 1 sweep) ---
-        # started from walker 0's configuration at the first timed sweep, with that sweep's
-        # random numbers, so that both paths solve equally conditioned matrices
-        if not args.no_plain:
+        #      same restored sweep, a fresh inverse at the restore --------------------------
+        if not over_budget():
+            t0 = time.perf_counter()
+            ctxd = make(vmc.PREC_FP64, vmc.ENGINE_DENSE_SM)
+            ms_d, sd_ = stationary_sweeps(ctxd, side_steps, 1)
+            extra["dense_sm_fp64_value"] = sum(x["proposals"] for x in sd_) / (sum(ms_d) / 1000.0)
+            vmc.vmc_destroy(ctxd)
+            log(f"dense: {time.perf_counter() - t0:.1f} s; {extra['dense_sm_fp64_value']:.0f} ratios/s")
+        else:
+            skipped.append("dense")
+        # ---- plain FP64 one-walker-per-launch path: walker 0's sweep S from the same state --
+        if not args.no_plain and not over_budget():
+            t0 = time.perf_counter()
             ctxp = make(vmc.PREC_FP64, vmc.ENGINE_PLAIN, nw=1)
-            vmc.vmc_set_positions(ctxp, 0, state["R0"])
-            vmc.vmc_set_sweep_count(ctxp, state["sweep"])
-            sd1 = seeds_dev[:1]
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            vmc.vmc_sweep_async(ctxp, 1, SIGMA, sd1)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            vmc.vmc_synchronize(ctxp)
-            plain = N / (e0.elapsed_time(e1) / 1000.0)
+            ms_p, sp_ = stationary_sweeps(ctxp, 1, 1, nw=1)
+            plain = sp_[0]["proposals"] / (ms_p[0] / 1000.0)
             vmc.vmc_destroy(ctxp)
             extra["plain_fp64_value"] = plain
-            extra["plain_fp64_sample"] = (f"walker 0 from its configuration at sweep {state['sweep']}, "
-                                          f"one sweep ({N} launches)")
+            extra["plain_fp64_sample"] = (f"walker 0, sweep {EQUIL_SWEEPS} from the saved state, {moves} launches "
+                                          f"(one per move), graph-replayed")
             extra["speedup_vs_plain"] = value / plain
-            extra["speedup_vs_plain_mixed"] = extra["mixed_value"] / plain
-    if rank == 0 and not args.no_kernels:
+            if "mixed_value" in extra:
+                extra["speedup_vs_plain_mixed"] = extra["mixed_value"] / plain
+            log(f"plain: {time.perf_counter() - t0:.1f} s; {plain:.0f} ratios/s")
+        elif not args.no_plain:
+            skipped.append("plain")
+    if rank == 0 and not args.no_kernels and not args.headline_only:
         # ---- per-kernel rooflines at the HBM-sized configurations (CTA per walker; n = 4096
         #      with 256 walkers, n = 32768 with 152 = one per SM): triangular solves and SpMV,
-        #      FP32 (mixed mode) ------------------------------------------------------------
+        #      FP32 (mixed mode); fixed repetition counts ----------------------------------
         hbm_peak, _ = peaks()
         kr = {}
-        # (K, walkers, kappa, r_c): n = 4096 with its configuration's 256 walkers; n = 32768 with
-        # 152 walkers, for the kappa = 2 / r_c = 1.5 matrices and for the large configuration's own
-        # kappa = 1 / r_c = 2 (about 33 entries a row)
         for K, nwk, kap, rc in ((16, 256, KAPPA, RC), (32, 152, KAPPA, RC), (32, 152, 1.0, 2.0)):
+            if over_budget():
+                skipped.append(f"kernels_sc{K}_k{kap:g}")
+                continue
+            t0 = time.perf_counter()
             ctxk = vmc.vmc_create([(K, 0, A, kap, rc)] * nwk, vmc.params(precision=vmc.PREC_MIXED), stream=stream)
             vmc.vmc_init_positions(ctxk, list(range(1, nwk + 1)), JITTER)
             reps = 40 if K == 16 else (10 if kap == KAPPA else 4)
@@ -405,6 +459,7 @@ def main():
                     "us_per_apply": 1000.0 * ms / reps, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": gbs / hbm_peak, "bytes_per_apply": by / reps}
             vmc.vmc_destroy(ctxk)
+            log(f"kernel rooflines sc{K} kappa {kap:g}: {time.perf_counter() - t0:.1f} s")
         extra["kernel_rooflines"] = kr
     if rank != 0:
         if world > 1:
@@ -414,38 +469,52 @@ def main():
     hbm, peak_kind = peaks()
     kernel_ms = total_ms / args.steps        # one sweep launch per step
     achieved = alg_bytes / args.steps / (kernel_ms / 1000.0) / 1e9
-    its = sum(s["inner_iterations"] for s in stats) / ratios_local
+    nprop = ratios_local
+    hist = [sum(s["its_hist"][b] for s in stats) for b in range(64)]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N, "walkers_per_gpu": WALKERS, "sweeps_per_step": 1,
-                   "engine": "persistent (one launch per sweep, CTA per walker)", "gmres_m": 30,
-                   "ilutp": "drop 1e-4, permtol 0.5", "inner_rtol": 1e-10, "refactorisation": refactoring,
-                   "l2": "256 MB buffer written between timed steps"},
+        "config": {"workload": WORKLOAD, "n": N, "walkers_per_gpu": NW, "moves_per_walker_per_step": moves,
+                   "step": f"moves 0..{moves - 1} of sweep {EQUIL_SWEEPS} of every walker, restored before every "
+                           f"step from the state after {EQUIL_SWEEPS} discarded sweeps (restore untimed)",
+                   "engine": "persistent (one launch per sweep)", "gmres_m": 30,
+                   "ilutp": "drop 1e-4, permtol 0.5", "inner_rtol": 1e-10, "trigger_rtol": 1e-6,
+                   "refactorisation": refactoring, "l2": "256 MB buffer written between timed steps",
+                   "side_legs": f"mixed and dense: {side_steps} timed + 1 warm-up restored sweeps; plain: one"},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": host_seeds.numel() * host_seeds.element_size(),
                 "d2h_bytes_per_step": acc_log.numel() * acc_log.element_size()
                 + rat_log.numel() * rat_log.element_size(),
-                "host_memory": host_memory, "api": "vmc_sweep (host seeds in, accept and ratio logs out)"},
+                "host_memory": host_memory,
+                "api": "vmc_sweep (host seeds in, accept and ratio logs out); the restore is outside the timing"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": profiled_traffic(f"{kernel_name}_sc10_n1000_w64_fp64.md"),
+                     "frac": achieved / hbm, "traffic": profiled_traffic(f"{kernel_name}_sc10_n1000_fp64.md"),
                      "note": f"{kernel_name}, algorithmic bytes from the kernel's per-phase counter; peak "
                              f"{peak_kind}"},
-        "solver": {"inner_its_per_ratio": its,
-                   "accept_rate": sum(s["accepts"] for s in stats) / ratios_local,
-                   "reorders": sum(s["reorders"] for s in stats),
-                   "refactorizations": sum(s["factorizations"] for s in stats)},
+        "solver": {"inner_its_per_ratio": sum(s["inner_iterations"] for s in stats) / nprop,
+                   "first_pass_its_per_ratio": sum(s["first_pass_iterations"] for s in stats) / nprop,
+                   "its_to_1e-6_per_ratio": sum(s["trigger_iterations"] for s in stats) / nprop,
+                   "outer_passes_per_ratio": sum(s["outer_passes"] for s in stats) / nprop,
+                   "accept_rate": sum(s["accepts"] for s in stats) / nprop,
+                   "reorders_per_1000_moves": 1000.0 * sum(s["reorders"] for s in stats) / nprop,
+                   "reorders_skipped_per_1000_moves": 1000.0 * sum(s["reorders_skipped"] for s in stats) / nprop,
+                   "factorizations_per_1000_moves": 1000.0 * sum(s["factorizations"] for s in stats) / nprop,
+                   "first_pass_its_hist": hist[:max(i for i, h in enumerate(hist) if h) + 1] if any(hist) else []},
+        "wall_s": time.perf_counter() - t_start,
     }
+    if skipped:
+        out["skipped_over_budget"] = skipped
     out.update(extra)
-    if not args.no_cpu_baseline and world == 1:  # timed on the host cores at N = 1 only
+    if not args.no_cpu_baseline and world == 1 and not args.headline_only:  # host cores, N = 1 only
         try:
             out["cpu_baseline"] = cpu_oracle_sample(6)[0]  # about 10 s on the host cores
             out["cpu_baseline_1core"] = cpu_oracle_sample(2, threads=1)[0]
         except Exception as e:  # the oracle is test infrastructure; report, do not fail
             out["cpu_baseline"] = {"value": None, "error": str(e)}
+    out["wall_s"] = time.perf_counter() - t_start
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

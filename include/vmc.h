@@ -119,6 +119,28 @@ typedef struct {
                           (with the sweep index kept on the device) and replay it once per
                           sweep (1), or launch them one by one (0).  Used when the call makes
                           one sweep or keeps no logs (1) */
+  double trigger_rtol; /* the controller's convergence test (Sec. 4: reorder when the iterative
+                          solver does not reach the required tolerance within the maximum number
+                          of iterations): the solve of a move counts as converged when its
+                          residual reaches trigger_rtol x ||e_i|| within trigger_its GMRES
+                          iterations, counted over all cycles (restarts and refinement passes).
+                          The solve itself always runs on to inner_rtol and the ratio goal;
+                          a failed test reorders and refactors for the moves that follow.
+                          <= 0: 1e-6, the paper's GMRES tolerance (1e-6) */
+  int trigger_its;     /* ... and its maximum iteration count; <= 0: 40, the paper's (40) */
+  int sweep_moves;     /* moves per sweep: 0 = every particle (a full sweep); m > 0 = only
+                          particles 0 .. m-1 of each walker (bounded partial sweeps for tests,
+                          diagnostics and autotuner trials; the log entries of particles not
+                          moved are left unwritten) (0) */
+  int ilutp_variant;   /* ILUTP implementation (same factors, bit for bit): 0 = auto: the
+                          working row in shared memory as a hash map keyed by label when the dense
+                          working row of n entries does not fit the walker CTA's shared memory
+                          (and n <= 65535), else the dense row; 1 = always the dense row; 2 =
+                          always the hash map where it fits (0) */
+  int trisolve_warp_rows; /* level-synchronous triangular solves: a level of at most this many
+                          rows, <= 32, is solved by one warp alone, with no barrier among the
+                          solving warps after it (the other warps meet it before the next larger
+                          level); 0 = every level by all solving warps (0) */
 } vmc_solver_params;
 
 /* Per-walker statistics (Sec. 4 Tables 2 and 3 analogues). */
@@ -158,6 +180,12 @@ typedef struct {
   int factor_set;            /* factor set in use (0 or 1)                                  */
   int async_lag;             /* the refactor_lag in effect (0: in-line refactorisation)     */
   int max_updates;           /* the max_updates in effect                                   */
+  int64_t trigger_iterations; /* GMRES iterations until the residual reached trigger_rtol, summed
+                                over solves (the paper's iteration count k1 at its tolerance 1e-6) */
+  int64_t reorders_skipped;  /* triggers (monitor, non-convergence, slow) that fired while the
+                                factors were those of a reorder + refactorisation of the very
+                                same matrix (no move accepted since): refactoring it again
+                                would reproduce them, so the solve only restarts           */
 } vmc_stats;
 
 /* Fill p (host) with the defaults above; VMC_ERR_INVALID for NULL. */
@@ -219,6 +247,14 @@ vmc_status vmc_init_positions(vmc_ctx* ctx, const uint64_t* seeds, double jitter
  * and status.  Errors: VMC_ERR_INVALID (NULL xyz, walker out of range, a non-finite
  * coordinate), VMC_ERR_CUDA, or the walker's failure status. */
 vmc_status vmc_set_positions(vmc_ctx* ctx, int walker, const double* xyz);
+/* vmc_set_positions for every walker at once (one set-up launch for the batch): xyz is
+ * host, walker-major, sum_w n_w*3 doubles (walker w's block starts at 3 (n_0 + ... +
+ * n_{w-1})), particle order within a block; wrapped into each walker's box.  Restores a
+ * saved batch state (with vmc_set_sweep_count) or starts every walker from given
+ * positions.  Resets every walker's statistics and status and drops pending ratios.
+ * Errors: VMC_ERR_INVALID (NULL xyz, a non-finite coordinate), VMC_ERR_CUDA, or the
+ * first failing walker's status. */
+vmc_status vmc_set_positions_all(vmc_ctx* ctx, const double* xyz);
 /* Copy walker w's current positions (particle order, in [0, L)) to xyz (host, n*3
  * doubles); synchronises the stream.  VMC_ERR_INVALID for bad arguments. */
 vmc_status vmc_get_positions(vmc_ctx* ctx, int walker, double* xyz);

@@ -1,8 +1,9 @@
 """In-tree build of the CUDA library ``libvmc.so`` for sm_103a (nvcc, no cmake).
 
-The four translation units (engine kernels; C ABI + host layout; the allocation-free
-entry point; the dense reference engine) compile in parallel and are
-linked into ``paper_1008_5113_gb300/libvmc.so`` next to this file.
+The translation units (the engine's kernels in FP64 and in FP32, the precision-independent
+launch entry points; C ABI + host layout; the allocation-free entry point; the dense
+reference engine) compile in parallel and are linked into
+``paper_1008_5113_gb300/libvmc.so`` next to this file.
 """
 from __future__ import annotations
 
@@ -16,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libvmc.so")
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["vmc_engine.cu", "vmc_capi.cu", "vmc_noalloc.cu", "vmc_dense.cu"]
+SOURCES = ["vmc_engine_f64.cu", "vmc_engine_f32.cu", "vmc_engine.cu", "vmc_capi.cu", "vmc_noalloc.cu", "vmc_dense.cu"]
 
 
 def _nvcc() -> str:

@@ -211,6 +211,11 @@ extern "C" vmc_status vmc_default_params(vmc_solver_params* p) {
   p->refactor_reorder = 0;
   p->trisolve = 0;
   p->graphs = 1;
+  p->trigger_rtol = 1e-6;
+  p->trigger_its = 40;
+  p->sweep_moves = 0;
+  p->ilutp_variant = 0;
+  p->trisolve_warp_rows = 0;
   return VMC_OK;
 }
 
@@ -329,6 +334,10 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   else if (!(p.drop_tol >= 0.0) || !(p.permtol >= 0.0) || p.max_restarts < 0) st = bad("ILUTP/GMRES parameters");
   else if (p.refactor_lag < -1) st = bad("refactor_lag must be >= -1");
   else if (p.trisolve < 0 || p.trisolve > 1) st = bad("trisolve must be 0 or 1");
+  else if (p.sweep_moves < 0) st = bad("sweep_moves must be >= 0");
+  else if (p.ilutp_variant < 0 || p.ilutp_variant > 2) st = bad("ilutp_variant must be 0, 1 or 2");
+  else if (p.trisolve_warp_rows < 0 || p.trisolve_warp_rows > 32) st = bad("trisolve_warp_rows must be in [0, 32]");
+  else if (!(p.trigger_rtol < 1.0)) st = bad("trigger_rtol must be below 1");
   if (st != VMC_OK) { *out = ctx; return st; }
   ctx->fp64 = p.precision == VMC_PREC_FP64;
   ctx->threads = p.block_threads ? p.block_threads : 256;
@@ -342,6 +351,11 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   ctx->P.ilu64 = p.precision != VMC_PREC_MIXED_F32ILU;
   ctx->P.N_max = p.N_max;
   ctx->P.slow_factor = p.slow_factor;
+  ctx->P.trig_rtol = p.trigger_rtol > 0.0 ? p.trigger_rtol : 1e-6;
+  ctx->P.trig_its = p.trigger_its > 0 ? p.trigger_its : 40;
+  ctx->P.step_limit = p.sweep_moves;
+  ctx->P.ilu_variant = p.ilutp_variant;
+  ctx->P.warp_rows = p.trisolve_warp_rows;
   {
     // background refactorisation (persistent engine) when asked for, or by default when
     // every walker pair fits and no system is larger than kAutoPairMaxN; the chain length
@@ -392,7 +406,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     const Layout& L = lay[w];
     const int n = L.n, cap = L.cap;
     const int pmax = p.lfil_extra >= 0 ? p.lfil_extra : (cap + 1) / 2;
-    const int capLU = cap + pmax + 2;
+    const int capLU = (cap + pmax + 2 + 3) / 4 * 4;  // rows of 16-byte multiples (bulk copies)
     auto& o = offs[w];
     o.push_back(cv.take<double>((size_t)n * 3));       // 0 Z
     o.push_back(cv.take<int>(n));                      // 1 col_of_orb
@@ -480,6 +494,8 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
       o.push_back(cv.take<int>(n));                    // 80 gP of the factor CTA
       o.push_back(cv.take<int>(n));                    // 81 gQ of the factor CTA
     }
+    o.push_back(cv.take<double2>(n));                  // u_head of factor set 0 (then of set 1)
+    if (ctx->pair) o.push_back(cv.take<double2>(n));
     Walker& W = ctx->hw[w];
     std::memset(&W, 0, sizeof(W));
     W.n = n; W.K = systems[w].K; W.lattice = systems[w].lattice; W.cap = cap; W.capLU = capLU;
@@ -581,6 +597,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     W.chunk_meta = (int4*)(A + o[47]);
     W.lvl_nchunk = (int*)(A + o[48]);
     W.seg_meta = (int4*)(A + o[49]);
+    W.u_head = (double2*)(A + o[ctx->pair ? 82 : 50]);
     W.ctl = ctx->dCtl + w;
     const Layout& L = lay[w];
     e = cudaMemcpyAsync((void*)W.Z, L.Z.data(), sizeof(double) * L.Z.size(), cudaMemcpyHostToDevice, ctx->stream);
@@ -627,6 +644,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
       W1.chunk_meta = (int4*)(A + o[71]);
       W1.lvl_nchunk = (int*)(A + o[72]);
       W1.seg_meta = (int4*)(A + o[73]);
+      W1.u_head = (double2*)(A + o[83]);
       W0.snap_len = (int*)(A + o[74]);
       W0.snap_col = (int*)(A + o[75]);
       W0.snap_val = (double*)(A + o[76]);
@@ -740,6 +758,28 @@ extern "C" vmc_status vmc_set_positions(vmc_ctx* ctx, int walker, const double* 
   CK(cudaMemcpyAsync(W.R, r.data(), sizeof(double) * r.size(), cudaMemcpyHostToDevice, ctx->stream), "positions");
   CK(cudaMemsetAsync(ctx->dCtl + walker, 0, sizeof(Ctl), ctx->stream), "reset walker");
   return setup_all(ctx, walker, 1);
+}
+
+extern "C" vmc_status vmc_set_positions_all(vmc_ctx* ctx, const double* xyz) {
+  if (!ctx || !xyz) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  std::vector<double> r;
+  size_t off = 0;
+  for (int w = 0; w < ctx->nw; ++w) {
+    const Walker& W = ctx->hw[w];
+    r.assign(xyz + off, xyz + off + (size_t)W.n * 3);
+    off += (size_t)W.n * 3;
+    for (double& v : r) {
+      if (!std::isfinite(v)) return fail(ctx, VMC_ERR_INVALID, "non-finite position (walker " + std::to_string(w) + ")");
+      double y = v - W.L * std::floor(v / W.L);
+      if (y >= W.L) y -= W.L;
+      v = y;
+    }
+    CK(cudaMemcpyAsync(W.R, r.data(), sizeof(double) * r.size(), cudaMemcpyHostToDevice, ctx->stream), "positions");
+    // the pageable source is reused for the next walker: let the copy take it first
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  }
+  CK(cudaMemsetAsync(ctx->dCtl, 0, sizeof(Ctl) * ctx->nw, ctx->stream), "reset walkers");
+  return setup_all(ctx, 0, ctx->nw);
 }
 
 extern "C" vmc_status vmc_get_positions(vmc_ctx* ctx, int walker, double* xyz) {
@@ -983,6 +1023,8 @@ extern "C" vmc_status vmc_get_stats(vmc_ctx* ctx, int walker, vmc_stats* out) {
   out->factor_set = h.active;
   out->async_lag = ctx->P.af_lag;
   out->max_updates = ctx->P.max_updates;
+  out->reorders_skipped = h.reorder_skipped;
+  out->trigger_iterations = h.trig_its;
   return VMC_OK;
 }
 
@@ -1001,6 +1043,8 @@ extern "C" vmc_status vmc_reset_stats(vmc_ctx* ctx) {
     c.alg_bytes = 0.0;
     c.ilu_rows = c.ilu_elims = c.ilu_cand = 0;
     c.refactors_async = c.af_wait_cyc = c.af_factor_cyc = 0;
+    c.reorder_skipped = 0;
+    c.trig_its = 0;
   }
   CK(cudaMemcpyAsync(ctx->dCtl, h.data(), sizeof(Ctl) * ctx->nw, cudaMemcpyHostToDevice, ctx->stream), "stats");
   CK(cudaStreamSynchronize(ctx->stream), "synchronize");

@@ -83,6 +83,12 @@ struct Ctl {
   int af_stop;        // launch id after which the factor CTA leaves
   int af_fail;        // the last background factorisation reported (bit 0 breakdown, bit 1 capacity)
   long long refactors_async, af_wait_cyc, af_factor_cyc;
+  // 1 while the factors in use come from a synchronous reorder + refactorisation of the
+  // current matrix (no move accepted and no background factors adopted since): a trigger
+  // then cannot be helped by refactoring, which would reproduce the same factors
+  int fresh;
+  long long reorder_skipped;
+  long long trig_its;  // iterations until the residual reached trig_rtol, summed over solves
 };
 
 // Immutable-per-context description of one walker: sizes and device pointers.
@@ -101,6 +107,7 @@ struct Walker {
   int* l_col; double* l_val64; int* l_len;
   int* u_col; double* u_val64; int* u_len;
   double* u_dinv64;
+  double2* u_head;        // per U row {1 / u_rr, length}, written by the shared-memory ILUTP (16 B: one bulk copy)
   // level-ordered chunk streams of L and U for the staged triangular solves
   unsigned char* lstream; unsigned char* ustream;
   int2* lchunk; int2* uchunk;   // per chunk {byte offset, bytes}
@@ -150,6 +157,10 @@ struct Params {
   int step_limit;   // > 0: a sweep moves only particles 0 .. step_limit - 1 (autotuner trials)
   int tri_sf;       // 1: synchronisation-free triangular solves (two solve vectors in shared memory)
   int y_half;       // byte offset of the second solve vector (tri_sf)
+  double trig_rtol; // controller: the solve converged if its residual reached this ...
+  int trig_its;     // ... within this many GMRES iterations (all cycles)
+  int ilu_variant;  // 0: auto (hash working row where the dense one misses shared memory); 1: dense; 2: hash
+  int warp_rows;    // levels of at most this many rows: triangular-solve rows by one warp, no barrier
 };
 
 // Shared memory of a walker CTA (static, < 48 KB).
@@ -182,7 +193,7 @@ struct __align__(16) Shared {
   int ucol[kMaxU];
   double cupd[kMaxUpd];
   int alen, ulen;
-  int iflag[8];
+  int iflag[12];
   double dflag[8];
 };
 

@@ -51,6 +51,35 @@ cudaError_t launch_dense_sweep(const LaunchCfg& L, const Walker* W, int nwalk, i
 cudaError_t launch_wait_timeout(int* status, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, cudaStream_t s);
 
+// Per-precision instantiations (vmc_engine_f64.cu, vmc_engine_f32.cu) behind the
+// launchers above.
+template <typename T> int kernel_static_smem_T();
+template <typename T>
+cudaError_t launch_sweep_T(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int n_sweeps,
+                           long long sweep0, double sigma, const uint64_t* seeds, uint8_t* acc, double* ratio);
+template <typename T>
+cudaError_t launch_sweep_pair_T(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P,
+                                int n_sweeps, long long sweep0, double sigma, const uint64_t* seeds, uint8_t* acc,
+                                double* ratio, int launch_id);
+template <typename T> cudaError_t prepare_step_kernels_T(const LaunchCfg& L);
+template <typename T>
+cudaError_t launch_step_T(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P, int q,
+                          int n_sweeps, int s_local, long long sweep0, double sigma, const uint64_t* seeds,
+                          uint8_t* acc, double* ratio, const long long* sweep_dev);
+template <typename T>
+cudaError_t launch_ratio_T(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int k, const double r[3],
+                           int want_grad);
+template <typename T>
+cudaError_t launch_kinetic_T(const LaunchCfg& L, const Walker* W, int nwalk, const Params& P, double* out);
+template <typename T> cudaError_t launch_accept_T(const LaunchCfg& L, const Walker* W, int wi, const Params& P);
+template <typename T>
+cudaError_t launch_setup_T(const LaunchCfg& L, const Walker* W, int walker0, int nwalk, const Params& P);
+template <typename T>
+cudaError_t launch_refactor_T(const LaunchCfg& L, const Walker* W, int wi, const Params& P, int reorder);
+template <typename T> cudaError_t launch_apply_precond_T(const LaunchCfg& L, const Walker* W, int wi, const Params& P);
+template <typename T>
+cudaError_t launch_bench_T(const LaunchCfg& L, const Walker* W, int nwalk, const Params& P, int which, int reps);
+
 // Shared-memory plan of a walker CTA: two solve vectors (2 ybytes) in shared memory
 // when they fit next to four ring slots and allow_sf (synchronisation-free triangular
 // solves), else one when it fits next to two slots, else none; then 16 KB slots when at

@@ -97,9 +97,8 @@ __device__ __forceinline__ void spmv(const Walker& w, const T* __restrict__ x, T
 // per kernel launch; chunk g of the launch lives in slot g % S, phase (g / S) & 1.
 __device__ __forceinline__ void ring_init(Shared& sh, const Params& P) {
   if (threadIdx.x == 0) {
-    // a slot is released by thread 0 (level-synchronous solves) or by every consumer
-    // warp (synchronisation-free solves)
-    const unsigned rel = P.tri_sf ? (unsigned)((blockDim.x >> 5) - 1) : 1u;
+    // a slot is released by every consumer warp once it is done with the chunk
+    const unsigned rel = (unsigned)((blockDim.x >> 5) - 1);
     for (int s = 0; s < P.ring_slots; ++s) {
       mbar_init(&sh.bar[s], 1);
       mbar_init(&sh.ebar[s], rel);
@@ -143,7 +142,10 @@ __device__ __forceinline__ long long stream_chunks(const unsigned char* stream, 
 // One triangular solve in place on y (shared or global), level-synchronous.  The last
 // warp produces (stream_chunks); the other warps solve: per chunk they wait for it to
 // land, solve its segments (levels) one after the other with a barrier among the
-// consumer warps between segments, and release the slot.
+// consumer warps between segments, and release the slot.  A segment marked for one
+// warp (few rows) is solved by the first consumer warp alone, with only a warp
+// synchronisation after it; the other consumer warps skip it and meet that warp at the
+// barrier before the next segment solved by all.
 // Lower: y_r -= sum_t L_rt y_t.  Upper: y_r = (y_r - sum_t U_rt y_t) / U_rr.
 // Every wait gives up after ~1 s (status VMC_ERR_TIMEOUT).
 template <typename T>
@@ -164,6 +166,7 @@ __device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, boo
     int slot = seq0 % S;
     unsigned parity = (unsigned)((seq0 / S) & 1);
     long long tdata = 0;
+    bool pend = false;  // the first warp solved rows the others have not synchronised with
     for (int c = 0; c < nch; ++c) {
       const long long tw0 = clock64();
       if (!mbar_wait(&sh.bar[slot], parity)) sh.iflag[3] = 1;
@@ -179,7 +182,42 @@ __device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, boo
       const T* dv = (const T*)((const unsigned char*)vl + pad16((int)sizeof(T) * ne));
       for (int sgi = 0; sgi < nseg; ++sgi) {
         const int4 sm = seg[sgi];
-        const int r0 = sm.x, sr = sm.y, gs = sm.z;
+        const int r0 = sm.x, sr = sm.y;
+        if (sm.w) {  // one warp
+          if (wid == 0) {
+            const int gs = sm.w - 1, G = 1 << gs, gl = lane & (G - 1);
+            const int i = r0 + (lane >> gs);
+            const bool on = (lane >> gs) < sr;
+            T part = 0;
+            int r = 0;
+            if (on) {
+              r = rws[i];
+              T part2 = 0;
+              const int e = st[i + 1];
+              int t = st[i] + gl;
+              for (; t + G < e; t += 2 * G) {
+                part += vl[t] * y[cl[t]];
+                part2 += vl[t + G] * y[cl[t + G]];
+              }
+              if (t < e) part += vl[t] * y[cl[t]];
+              part += part2;
+            }
+            for (int o = G >> 1; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o, G);
+            if (on && gl == 0) {
+              T acc = y[r] - part;
+              if (upper) acc *= dv[i];
+              y[r] = acc;
+            }
+            __syncwarp();
+          }
+          pend = true;
+          continue;
+        }
+        if (pend) {  // publish the first warp's rows before a segment solved by all
+          asm volatile("bar.sync 1, %0;" ::"r"(nct) : "memory");
+          pend = false;
+        }
+        const int gs = sm.z;
         const int G = 1 << gs;
         const int gl = tid & (G - 1);
         const int ng = nct >> gs;
@@ -209,7 +247,8 @@ __device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, boo
         }
         asm volatile("bar.sync 1, %0;" ::"r"(nct) : "memory");  // level barrier (consumers)
       }
-      if (tid == 0) mbar_arrive(&sh.ebar[slot]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.ebar[slot]);  // this warp is done with the chunk
       if (++slot == S) { slot = 0; parity ^= 1u; }
     }
     if (tid == 0) w.ctl->cyc[PH_TRIDATA] += tdata;
@@ -475,16 +514,18 @@ __device__ __forceinline__ void multi_dot(const T* __restrict__ V, int n, int nk
 }
 
 // Right-preconditioned GMRES(m) on A_p M d = rhs (FP64 rhs, norm beta); adds the
-// correction M V y into x64.  Returns the iteration count; conv and the monitor N.
+// correction M V y into x64.  Returns the iteration count; conv (reached rtol), the
+// monitor N and, when its_trig is given, the iteration at which the residual estimate
+// first reached trig * beta (-1: not in this cycle; the controller's convergence test).
 template <typename T>
 __device__ __noinline__ int gmres_inner(const Walker& w, const Params& P, double beta, double rtol, bool& conv,
-                           double& Nmon, Shared& sh) {
+                           double& Nmon, Shared& sh, double trig = 0.0, int* its_trig = nullptr) {
   const int n = w.n, tid = threadIdx.x, nt = blockDim.x, m = P.m;
   T* V = (T*)w.V;
   T* Zk = (T*)w.Zk;
   const double inv = 1.0 / beta;
   for (int i = tid; i < n; i += nt) V[i] = (T)(w.r64[i] * inv);
-  if (tid == 0) { sh.g[0] = beta; sh.iflag[1] = 0; }
+  if (tid == 0) { sh.g[0] = beta; sh.iflag[1] = 0; sh.iflag[8] = -1; }
   double mon2 = 0.0;
   __syncthreads();
   int j = 0;
@@ -542,6 +583,7 @@ __device__ __noinline__ int gmres_inner(const Walker& w, const Params& P, double
       sh.g[j + 1] = -sh.sn[j] * sh.g[j];
       sh.g[j] = sh.cs[j] * sh.g[j];
       sh.iflag[1] = (fabs(sh.g[j + 1]) <= rtol * beta) || nrm == 0.0;
+      if (sh.iflag[8] < 0 && fabs(sh.g[j + 1]) <= trig * beta) sh.iflag[8] = j + 1;
       w.ctl->cyc[PH_ORTH] += clock64() - to;
     }
     __syncthreads();
@@ -549,6 +591,7 @@ __device__ __noinline__ int gmres_inner(const Walker& w, const Params& P, double
     if (sh.iflag[1]) break;
   }
   conv = sh.iflag[1] != 0;
+  if (its_trig) *its_trig = sh.iflag[8];
   Nmon = sqrt(mon2);
   if (tid == 0) {
     const double* H = sh.H;
@@ -603,8 +646,9 @@ __device__ __forceinline__ double u_dot_x(const Walker& w, Shared& sh) {
 
 struct SolveOut {
   double ratio;
-  int its1;
-  bool conv1;
+  int its1;          // iterations of the first cycle
+  bool conv1;        // the first cycle reached its tolerance
+  int its_trig;      // iterations (all cycles) until the residual reached Params::trig_rtol; -1: never
   double N;
   int passes;
   int total_its;
@@ -623,8 +667,10 @@ __device__ void solve_first(const Walker& w, const Params& P, int brow, double r
   __syncthreads();
   bool conv = false;
   double N = 0.0;
-  o.its1 = gmres_inner<T>(w, P, 1.0, rtol, conv, N, sh);
+  int at = -1;
+  o.its1 = gmres_inner<T>(w, P, 1.0, rtol, conv, N, sh, P.trig_rtol, &at);
   o.conv1 = conv;
+  o.its_trig = at;
   o.N = N;
   o.total_its = o.its1;
   o.passes = 1;
@@ -649,6 +695,8 @@ __device__ __noinline__ void refine(const Walker& w, const Params& P, int brow, 
   double rn = residual64(w, brow, &xn, sh);
   o.status = ST_OK;
   for (;;) {
+    // ||e_r|| = 1: the FP64 residual norm is also the relative residual
+    if (o.its_trig < 0 && rn <= P.trig_rtol) o.its_trig = o.total_its;
     const double delta = fabs(ratio - ratio_prev);
     const double pred = fmax(delta * rn / rprev, unorm * xn * rn);
     const double goal = P.ratio_tol * fmax(fabs(ratio), 1e-3);
@@ -661,7 +709,9 @@ __device__ __noinline__ void refine(const Walker& w, const Params& P, int brow, 
     need = fmin(fmax(need, rtol_floor), 0.1);
     bool conv = false;
     double N = 0.0;
-    const int its = gmres_inner<T>(w, P, rn, need, conv, N, sh);
+    int at = -1;
+    const int its = gmres_inner<T>(w, P, rn, need, conv, N, sh, P.trig_rtol / rn, &at);
+    if (o.its_trig < 0 && at > 0) o.its_trig = o.total_its + at;
     o.total_its += its;
     o.passes += 1;
     ratio_prev = ratio;

@@ -11,9 +11,11 @@
 // fixed size, kNoAllocBytes, which every GPU that loads the library holds until
 // the process exits.  The caller passes the inputs and the output.
 //
-// The device address of that array is looked up once per device with
-// cudaGetSymbolAddress, on the first call made with that device current; that
-// first call should therefore come before any stream capture.  Every call reuses
+// The device address of that array is looked up with cudaGetSymbolAddress on the
+// first call made with a device current, and again whenever that device's context
+// has changed since (after a cudaDeviceReset the module is loaded anew, possibly at
+// another address); the first call on a device should therefore come before any
+// stream capture.  Every call reuses
 // the same array and overwrites the previous call's contents (the used part is
 // cleared at the start of each call), so calls that overlap on the GPU -- on
 // different streams or from different host threads -- race and must not be issued.
@@ -40,20 +42,42 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_mu;
 unsigned char* g_scratch_addr[kMaxDevices] = {};
+void* g_scratch_ctx[kMaxDevices] = {};  // the context the address belongs to
 thread_local std::string g_noalloc_error;
 
-// Device address of the scratch array for the current device (looked up once).
+// The driver's cuCtxGetCurrent, reached through the runtime (no link against libcuda).
+using CtxGetCurrentFn = int (*)(void**);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return (CtxGetCurrentFn)f;
+  }();
+  return fn;
+}
+
+// Device address of the scratch array for the current device: looked up on the first
+// call with this device current, and again when the device's context has changed.
 cudaError_t scratch_address(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  const CtxGetCurrentFn get = ctx_get_current();
+  if (!get) return cudaErrorDeviceUninitialized;
+  void* cur = nullptr;
+  if (get(&cur) != 0) cur = nullptr;  // null before the runtime has made a context current
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_addr[dev]) {
+  if (!cur || !g_scratch_addr[dev] || g_scratch_ctx[dev] != cur) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // initialises the context if need be
     if (e != cudaSuccess) return e;
+    if (get(&cur) != 0 || !cur) return cudaErrorDeviceUninitialized;
     g_scratch_addr[dev] = (unsigned char*)p;
+    g_scratch_ctx[dev] = cur;
   }
   *out = g_scratch_addr[dev];
   return cudaSuccess;
@@ -107,7 +131,7 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   const size_t Tsz = fp64 ? sizeof(double) : sizeof(float);
   const int m = p.gmres_m, mu = std::max(1, p.max_updates);
   const int pmax = p.lfil_extra >= 0 ? p.lfil_extra : (cap + 1) / 2;
-  const int capLU = cap + pmax + 2;
+  const int capLU = (cap + pmax + 2 + 3) / 4 * 4;
   const size_t sbytes = (size_t)n * (256 + 12 * (size_t)capLU);
 
   // carve the walker workspace out of the scratch array
@@ -133,6 +157,7 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   const size_t oPac = o.take<int>(cap), oPav = o.take<double>(cap), oPuc = o.take<int>(kMaxU);
   const size_t oPuv = o.take<double>(kMaxU), oMeta = o.take<int4>(n + 1), oLnc = o.take<int>(n + 1);
   const size_t oSeg = o.take<int4>(2 * (size_t)n + 2);
+  const size_t oUh = o.take<double2>(n);
   const size_t oCtl = o.take<Ctl>(1), oW = o.take<Walker>(1);
   const size_t used = o.off;
   if (used > kNoAllocBytes)
@@ -155,6 +180,7 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   W.l_col = (int*)(base + oLc); W.l_val64 = (double*)(base + oLv); W.lstream = base + oLs; W.l_len = (int*)(base + oLl);
   W.u_col = (int*)(base + oUc); W.u_val64 = (double*)(base + oUv); W.ustream = base + oUs; W.u_len = (int*)(base + oUl);
   W.u_dinv64 = (double*)(base + oUd);
+  W.u_head = (double2*)(base + oUh);
   W.lchunk = (int2*)(base + oCh); W.uchunk = W.lchunk + (n + 1);
   W.perm = (int*)(base + oPm); W.iperm = (int*)(base + oIp); W.lev_l = (int*)(base + oLvl); W.lev_u = (int*)(base + oUvl);
   W.l_lvl_ptr = (int*)(base + oLlp); W.l_lvl_rows = (int*)(base + oLlr);
@@ -178,6 +204,11 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   P.ratio_tol = p.ratio_tol > 0.0 ? p.ratio_tol : 1e-12;
   P.ilu64 = p.precision != VMC_PREC_MIXED_F32ILU;
   P.N_max = p.N_max; P.slow_factor = p.slow_factor;
+  P.trig_rtol = p.trigger_rtol > 0.0 ? p.trigger_rtol : 1e-6;
+  P.trig_its = p.trigger_its > 0 ? p.trigger_its : 40;
+  P.ilu_variant = (p.ilutp_variant >= 0 && p.ilutp_variant <= 2) ? p.ilutp_variant : 0;
+  P.warp_rows = std::min(std::max(p.trisolve_warp_rows, 0), 32);
+  P.step_limit = 0;
   // shared-memory plan for a single walker CTA
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);

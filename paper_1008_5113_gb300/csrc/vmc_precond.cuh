@@ -20,7 +20,7 @@ namespace vmc {
 // new partner particle, so only part_of_row / row_of_part change.
 // Block-wide; O(n^2) distance evaluations.
 // ---------------------------------------------------------------------------
-__device__ __noinline__ void reorder_block(const Walker& w, Shared& sh) {
+static __device__ __noinline__ void reorder_block(const Walker& w, Shared& sh) {
   const int n = w.n, tid = threadIdx.x, nt = blockDim.x;
   for (int c = tid; c < n; c += nt) { w.gP[c] = w.part_of_row[c]; w.gQ[c] = w.orb_of_col[c]; }
   __syncthreads();
@@ -507,6 +507,403 @@ __device__ __noinline__ int ilutp_warp(const Walker& w, const Params& P, Shared&
 }
 
 // ---------------------------------------------------------------------------
+// ILUTP with the working row in shared memory (the same elimination, drop, lfil and
+// pivot rules as ilutp_warp, in the same order, so the factors are the same).
+//   * The working row is an open-addressing hash map keyed by factor label (linear
+//     probing, a table of HS slots for at most HS/2 candidates): its entries' labels in
+//     sh.nz[t], values in wv[t], hash slot in hslot[t].
+//   * The inverse column permutation is held in shared memory as 16-bit labels
+//     (n <= 65535).
+//   * A U row is read with its header {1/u_rr, length} (u_head) in one round trip: the
+//     lanes load the header and the row's first 64 slots together, before the length
+//     is known.  When shared memory is left over (small n) the finished U rows, their
+//     inverse diagonals and lengths are also cached there, as in ilutp_warp.
+// One warp; the caller synchronises the block afterwards.  Returns the ilutp_warp flags.
+// ---------------------------------------------------------------------------
+struct IluSm {
+  int ok, HS, lgHS, maxc, cache;
+  unsigned o_bits, o_sum, o_ip, o_hkey, o_hidx, o_hslot, o_wv, o_meta, o_len, o_uoff, o_cc, ucap;
+};
+template <typename T>
+__device__ __forceinline__ IluSm ilu_sm_plan(int n, size_t dbytes) {
+  IluSm pl{};
+  pl.ok = 0;
+  if (n > 65535) return pl;
+  const unsigned nwords = (n + 31) >> 5, nsum = (nwords + 31) >> 5;
+  for (int lg = 12; lg >= 11; --lg) {
+    const unsigned HS = 1u << lg, maxc = min((int)(HS / 2), kMaxRowNZ);
+    unsigned o = 0;
+    pl.o_bits = o; o += 4u * pad4(nwords);
+    pl.o_sum = o; o += 4u * pad4(nsum);
+    pl.o_ip = o; o += pad16(2 * n);
+    pl.o_hkey = o; o += 4u * HS;
+    pl.o_hidx = o; o += 2u * HS;
+    pl.o_hslot = o; o += pad16(2 * maxc);
+    pl.o_wv = o; o += pad16((int)sizeof(T) * maxc);
+    if (o > dbytes) continue;
+    pl.ok = 1; pl.HS = (int)HS; pl.lgHS = lg; pl.maxc = (int)maxc;
+    // U-row cache: inverse diagonals, lengths and row offsets, then rows of (column, value)
+    pl.o_meta = o;
+    const unsigned mo = o + pad16((int)sizeof(T) * n);
+    pl.o_len = mo;
+    pl.o_uoff = mo + pad16(2 * n);
+    pl.o_cc = pl.o_uoff + 4u * pad4(n + 1);
+    pl.cache = 0;
+    if (pl.o_cc + 64u * (4u + sizeof(T)) <= dbytes) {
+      pl.cache = 1;
+      pl.ucap = (unsigned)((dbytes - pl.o_cc) / (4u + sizeof(T))) & ~3u;
+    }
+    return pl;
+  }
+  return pl;
+}
+
+template <typename T>
+__device__ __noinline__ int ilutp_warp_hash(const Walker& w, const Params& P, Shared& sh, const IluSm pl,
+                                            int* npiv_out, double* nnz_out, int* p_out) {
+  const int n = w.n, lane = threadIdx.x & 31, cap = w.cap, capLU = w.capLU;
+  unsigned char* dsm = dyn_smem();
+  unsigned* lbits = (unsigned*)(dsm + pl.o_bits);
+  unsigned* lsum = (unsigned*)(dsm + pl.o_sum);
+  unsigned short* ip = (unsigned short*)(dsm + pl.o_ip);
+  int* hkey = (int*)(dsm + pl.o_hkey);
+  unsigned short* hidx = (unsigned short*)(dsm + pl.o_hidx);
+  unsigned short* hslot = (unsigned short*)(dsm + pl.o_hslot);
+  T* wv = (T*)(dsm + pl.o_wv);
+  const bool cache = pl.cache != 0;
+  T* mdinv = (T*)(dsm + pl.o_meta);                  // cache: 1 / u_rr per row
+  unsigned short* mlen = (unsigned short*)(dsm + pl.o_len);
+  int* uoff = (int*)(dsm + pl.o_uoff);               // cache: row offset, or -1
+  int* ucc = (int*)(dsm + pl.o_cc);
+  T* ucv = (T*)(ucc + pl.ucap);
+  const int ucap = cache ? (int)pl.ucap : 0;
+  int ufill = 0;
+  const int HS = pl.HS, hmask = HS - 1, hshift = 32 - pl.lgHS, MAXC = pl.maxc;
+  const int nwords = (n + 31) >> 5, nsum = (nwords + 31) >> 5;
+  for (int i = lane; i < nwords; i += 32) lbits[i] = 0u;
+  for (int i = lane; i < nsum; i += 32) lsum[i] = 0u;
+  for (int i = lane; i < HS; i += 32) hkey[i] = -1;
+  for (int i = lane; i < n; i += 32) { w.perm[i] = i; ip[i] = (unsigned short)i; w.lev_l[i] = 0; }
+  __syncwarp();
+  int p = P.lfil_extra;
+  if (p < 0) {
+    long long tot = 0;
+    for (int i = lane; i < n; i += 32) tot += w.a_len[i];
+    tot = warp_sum_ll(tot);
+    p = (int)((tot + 2LL * n - 1) / (2LL * n));  // ceil(avg nnz per row / 2)
+  }
+  p = min(p, (capLU - 2) / 2);
+  const int pk = max(0, min(p, capLU - 2 - cap));
+  int flags = 0, npiv = 0;
+  long long n_elim = 0, n_cand = 0;
+  double nnz = 0.0;
+  auto hash_of = [&](int f) -> int { return (int)(((unsigned)f * 0x9E3779B1u) >> hshift); };
+  // index of label f in the working row, or -1 (every lane the same)
+  auto find = [&](int f) -> int {
+    int h = hash_of(f);
+    for (int probe = 0; probe < HS; ++probe) {
+      const int k = hkey[h];
+      if (k == f) { const int t = hidx[h]; return t == 0xFFFF ? -1 : t; }
+      if (k == -1) return -1;
+      h = (h + 1) & hmask;
+    }
+    return -1;
+  };
+  for (int r = 0; r < n; ++r) {
+    const int part = w.part_of_row[r];
+    const int len = w.a_len[part];
+    const int* ac = w.a_col + (size_t)part * cap;
+    const double* av = w.a_val + (size_t)part * cap;
+    double ss = 0.0;
+    int nl = 0, nu = 0;
+    for (int t = lane; t < len; t += 32) {  // distinct labels: plain inserts
+      const int f = ip[ac[t]];
+      const double v = av[t];
+      int h = hash_of(f);
+      for (int probe = 0; probe < HS; ++probe) {
+        if (atomicCAS(&hkey[h], -1, f) == -1) break;
+        h = (h + 1) & hmask;
+      }
+      hidx[h] = (unsigned short)t;
+      hslot[t] = (unsigned short)h;
+      sh.nz[t] = f;
+      wv[t] = (T)v;
+      ss += v * v;
+      nl += f < r;
+      nu += f > r;
+      if (f < r) {
+        atomicOr(&lbits[f >> 5], 1u << (f & 31));
+        atomicOr(&lsum[f >> 10], 1u << ((f >> 5) & 31));
+      }
+    }
+    ss = warp_sum(ss);
+    nl = warp_sum_int(nl);
+    nu = warp_sum_int(nu);
+    int cnt = len;
+    const double norm = sqrt(ss);
+    const T thr = (T)(P.drop_tol * norm);
+    __syncwarp();
+    // --- elimination with the previous U rows, in increasing label order ---
+    int last = -1;
+    for (;;) {
+      int best = 0x7fffffff;
+      __syncwarp();
+      {
+        // next pending label > last: first the rest of last's word, then the summary
+        const int w0 = (last + 1) >> 5;
+        const unsigned cur = w0 < nwords ? lbits[w0] & (0xffffffffu << ((last + 1) & 31)) : 0u;
+        if (cur) {
+          best = (w0 << 5) + __ffs(cur) - 1;
+        } else {
+          const int s0 = (w0 + 1) >> 5;  // summary word holding bitmap word w0 + 1
+          for (int sb = s0; sb < nsum && best == 0x7fffffff; sb += 32) {
+            const int si = sb + lane;
+            unsigned sv = si < nsum ? lsum[si] : 0u;
+            if (si == s0) sv &= 0xffffffffu << ((w0 + 1) & 31);
+            const unsigned any = __ballot_sync(0xffffffffu, sv != 0u);
+            if (any) {
+              const int src = __ffs(any) - 1;
+              const unsigned svs = __shfl_sync(0xffffffffu, sv, src);
+              const int word = ((sb + src) << 5) + __ffs(svs) - 1;
+              best = (word << 5) + __ffs(lbits[word]) - 1;
+            }
+          }
+        }
+      }
+      if (best >= r) break;
+      last = best;
+      ++n_elim;
+      // the U row of best: header and first 64 slots in one round trip (or the cache)
+      const int ub = cache ? uoff[best] : -1;
+      T dinv;
+      int ul;
+      int c0 = 0, c1 = 0;
+      T v0 = 0, v1 = 0;
+      if (ub >= 0) {
+        dinv = mdinv[best];
+        ul = mlen[best];
+        if (lane < ul) { c0 = ucc[ub + lane]; v0 = ucv[ub + lane]; }
+        if (lane + 32 < ul) { c1 = ucc[ub + lane + 32]; v1 = ucv[ub + lane + 32]; }
+      } else {
+        const size_t rb = (size_t)best * capLU;
+        const double2 hd = w.u_head[best];
+        if (lane < capLU) { c0 = w.u_col[rb + lane]; v0 = (T)w.u_val64[rb + lane]; }
+        if (lane + 32 < capLU) { c1 = w.u_col[rb + lane + 32]; v1 = (T)w.u_val64[rb + lane + 32]; }
+        dinv = (T)hd.x;
+        ul = (int)hd.y;
+      }
+      const int tb = find(best);
+      const T wk = wv[tb] * dinv;
+      __syncwarp();
+      if (fabs(wk) < thr) {
+        if (lane == 0) wv[tb] = (T)0;  // dropped multiplier
+        continue;
+      }
+      if (lane == 0) wv[tb] = wk;
+      for (int base = 0; base < ul; base += 32) {
+        const int t = base + lane;
+        const bool valid = t < ul;
+        int f = 0, h = 0, ex = -1;
+        T v = 0;
+        bool ins = false;
+        if (valid) {
+          int c;
+          if (base == 0) { c = c0; v = v0; }
+          else if (base == 32) { c = c1; v = v1; }
+          else if (ub >= 0) { c = ucc[ub + t]; v = ucv[ub + t]; }
+          else { c = w.u_col[(size_t)best * capLU + t]; v = (T)w.u_val64[(size_t)best * capLU + t]; }
+          f = ip[c];
+          h = hash_of(f);
+          for (int probe = 0; probe < HS; ++probe) {
+            const int k = hkey[h];
+            if (k == f) { ex = hidx[h]; break; }
+            if (k == -1) {
+              const int old = atomicCAS(&hkey[h], -1, f);
+              if (old == -1) { ins = true; break; }
+              if (old == f) { ex = hidx[h]; break; }
+            }
+            h = (h + 1) & hmask;
+          }
+        }
+        const unsigned nm = __ballot_sync(0xffffffffu, ins);
+        const int slot_i = cnt + __popc(nm & lanemask_lt());
+        if (ins) {
+          if (slot_i < MAXC) {
+            hidx[h] = (unsigned short)slot_i;
+            hslot[slot_i] = (unsigned short)h;
+            sh.nz[slot_i] = f;
+            wv[slot_i] = -wk * v;
+            if (f < r) {
+              atomicOr(&lbits[f >> 5], 1u << (f & 31));
+              atomicOr(&lsum[f >> 10], 1u << ((f >> 5) & 31));
+            }
+          } else {
+            hidx[h] = 0xFFFF;  // over capacity: the factorisation is flagged unusable
+          }
+        } else if (valid && ex >= 0 && ex != 0xFFFF) {
+          wv[ex] -= wk * v;
+        }
+        cnt += __popc(nm);
+        __syncwarp();
+      }
+      if (cnt > MAXC) { flags |= 2; cnt = MAXC; }
+    }
+    n_cand += cnt;
+    // --- L part: keep the nl + p largest multipliers ---
+    T* selv = reinterpret_cast<T*>(sh.selV);
+    int cL = 0;
+    for (int base = 0; base < cnt; base += 32) {
+      const int t = base + lane;
+      bool c = false;
+      int f = 0;
+      T v = 0;
+      if (t < cnt) { f = sh.nz[t]; v = wv[t]; c = f < r && v != (T)0; }
+      const unsigned m = __ballot_sync(0xffffffffu, c);
+      const int slot = cL + __popc(m & lanemask_lt());
+      if (c && slot < kMaxSel) { sh.selF[slot] = f; selv[slot] = v; }
+      cL += __popc(m);
+    }
+    if (cL > kMaxSel) { flags |= 2; cL = kMaxSel; }
+    __syncwarp();
+    const int keepL = nl + pk;
+    select_topk<T>(sh, cL, keepL);
+    int nL = 0, levmax = -1;
+    for (int base = 0; base < cL; base += 32) {
+      const int e = base + lane;
+      const bool k = e < cL && sh.selK[e];
+      const unsigned m = __ballot_sync(0xffffffffu, k);
+      const int slot = nL + __popc(m & lanemask_lt());
+      if (k && slot < capLU) {
+        w.l_col[(size_t)r * capLU + slot] = sh.selF[e];
+        w.l_val64[(size_t)r * capLU + slot] = (double)selv[e];
+        levmax = max(levmax, w.lev_l[sh.selF[e]]);
+      }
+      nL += __popc(m);
+    }
+    levmax = warp_max_int(levmax);
+    if (nL > capLU) { flags |= 2; nL = capLU; }
+    __syncwarp();
+    // --- U part: entries above threshold, keep the nu + p largest ---
+    const int td = find(r);
+    T dval = td >= 0 ? wv[td] : (T)0;
+    int cU = 0;
+    for (int base = 0; base < cnt; base += 32) {
+      const int t = base + lane;
+      bool c = false;
+      int f = 0;
+      T v = 0;
+      if (t < cnt) { f = sh.nz[t]; v = wv[t]; c = f > r && fabs(v) >= thr && v != (T)0; }
+      const unsigned m = __ballot_sync(0xffffffffu, c);
+      const int slot = cU + __popc(m & lanemask_lt());
+      if (c && slot < kMaxSel) { sh.selF[slot] = f; selv[slot] = v; }
+      cU += __popc(m);
+    }
+    if (cU > kMaxSel) { flags |= 2; cU = kMaxSel; }
+    __syncwarp();
+    const int keepU = nu + pk;
+    select_topk<T>(sh, cU, keepU);
+    bool mykeep[kMaxSel / 32];
+#pragma unroll
+    for (int q = 0; q < kMaxSel / 32; ++q) {
+      const int e = q * 32 + lane;
+      mykeep[q] = e < cU && sh.selK[e];
+    }
+    __syncwarp();
+    // pivot: the largest kept U entry (ties: smaller label)
+    T bv = 0;
+    int bf = 0x7fffffff;
+#pragma unroll
+    for (int q = 0; q < kMaxSel / 32; ++q) {
+      const int e = q * 32 + lane;
+      if (mykeep[q]) {
+        const T v = fabs(selv[e]);
+        const int f = sh.selF[e];
+        if (v > bv || (v == bv && f < bf)) { bv = v; bf = f; }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const T v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int f2 = __shfl_xor_sync(0xffffffffu, bf, o);
+      if (v2 > bv || (v2 == bv && f2 < bf)) { bv = v2; bf = f2; }
+    }
+    int jm = -1;
+    if (bf != 0x7fffffff && (T)P.permtol * bv > fabs(dval)) jm = bf;
+    T newdiag = dval;
+    if (jm >= 0) {
+      // the column labelled jm becomes the diagonal; the old diagonal value moves
+      // to label jm (a U-part entry, or nothing if it was zero)
+      newdiag = wv[find(jm)];
+      if (lane == 0) {
+        const int cr = w.perm[r], cj = w.perm[jm];
+        w.perm[r] = cj; w.perm[jm] = cr;
+        ip[cj] = (unsigned short)r; ip[cr] = (unsigned short)jm;
+      }
+      ++npiv;
+    }
+    __syncwarp();
+    int nU = 0;
+#pragma unroll
+    for (int q = 0; q < kMaxSel / 32; ++q) {
+      const int e = q * 32 + lane;
+      bool k = mykeep[q];
+      T v = 0;
+      int f = 0;
+      if (k) {
+        f = sh.selF[e];
+        v = selv[e];
+        if (f == jm) { v = dval; k = dval != (T)0; }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, k);
+      const int slot = nU + __popc(m & lanemask_lt());
+      if (k && slot < capLU) {
+        const int oc = w.perm[f];  // original column label
+        w.u_col[(size_t)r * capLU + slot] = oc;
+        w.u_val64[(size_t)r * capLU + slot] = (double)v;
+        if (cache && ufill + slot < ucap) { ucc[ufill + slot] = oc; ucv[ufill + slot] = v; }
+      }
+      nU += __popc(m);
+    }
+    if (nU > capLU) { flags |= 2; nU = capLU; }
+    if (newdiag == 0.0) {
+      newdiag = (1e-4 + P.drop_tol) * (norm > 0.0 ? norm : 1.0);
+      flags |= 1;
+    }
+    if (lane == 0) {
+      const T di = (T)(1.0 / newdiag);
+      w.l_len[r] = nL;
+      w.u_len[r] = nU;
+      w.u_dinv64[r] = (double)di;
+      w.u_head[r] = make_double2((double)di, (double)nU);
+      w.lev_l[r] = levmax + 1;
+      if (cache) {
+        mdinv[r] = di;
+        mlen[r] = (unsigned short)nU;
+        uoff[r] = ufill + nU <= ucap ? ufill : -1;
+      }
+    }
+    if (cache && ufill + nU <= ucap) ufill += nU;
+    nnz += (double)(nL + nU + 1);
+    // clear the working row (and the pending-label bitmaps)
+    for (int t = lane; t < cnt; t += 32) {
+      const int f = sh.nz[t];
+      hkey[hslot[t]] = -1;
+      if (f < r) { lbits[f >> 5] = 0u; lsum[f >> 10] = 0u; }
+    }
+    if (flags & 2)  // keys past the capacity have no slot record: clear the whole table
+      for (int i = lane; i < HS; i += 32) hkey[i] = -1;
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) w.iperm[i] = ip[i];
+  __syncwarp();
+  if (lane == 0) { w.ctl->ilu_rows += n; w.ctl->ilu_elims += n_elim; w.ctl->ilu_cand += n_cand; }
+  *npiv_out = npiv;
+  *nnz_out = nnz;
+  *p_out = p;
+  return flags;
+}
+
+// ---------------------------------------------------------------------------
 // Level-ordered chunk stream of one triangular factor, consumed by the staged
 // solve.  Consecutive levels are packed into a chunk (one segment each) while it
 // stays within the slot size and kMaxSeg segments; a level larger than a slot is
@@ -554,7 +951,16 @@ __device__ int build_stream(const Walker& w, const Params& P, bool upper, int nl
     for (int lev = 0; lev < nlev; ++lev) {
       int q = lptr[lev];
       const int qe = lptr[lev + 1];
-      const int lr = qe - q, le = w.lvl_nchunk[lev] & ((1 << 28) - 1), lgs = w.lvl_nchunk[lev] >> 28;
+      const int lr = qe - q, le = w.lvl_nchunk[lev] & ((1 << 28) - 1);
+      // levels of at most P.warp_rows rows are solved by one warp alone, with no barrier
+      // among the solving warps; the segment records 1 + log2 of that warp's lanes per row
+      // (0: all warps).  Decided per level, so that pieces of a level split over chunks
+      // round alike.
+      const int gsl = w.lvl_nchunk[lev] >> 28;
+      int gw = gsl;
+      while (gw > 0 && (lr << gw) > 32) --gw;
+      const int wmode = (lr <= P.warp_rows && (lr << gw) <= 32) ? gw + 1 : 0;
+      const int lgs = gsl | (wmode << 8);
       if (cs < kMaxSeg && chunk_bytes(cs + 1, cr + lr, ce + le, tsz, upper) <= SB) {
         w.seg_meta[nseg++] = make_int4(q, lr, le, lgs);  // the whole level joins the open chunk
         ++cs; cr += lr; ce += le;
@@ -613,7 +1019,7 @@ __device__ int build_stream(const Walker& w, const Params& P, bool upper, int nl
     for (int sgi = 0; sgi < nseg; ++sgi) {
       const int4 sm = w.seg_meta[seg0 + sgi];
       const int q0 = sm.x, sr = sm.y;
-      if (lane == 0) seg[sgi] = make_int4(rbase, sr, sm.w, 0);
+      if (lane == 0) seg[sgi] = make_int4(rbase, sr, sm.w & 0xff, sm.w >> 8);
       for (int b0 = 0; b0 < sr; b0 += 32) {
         const int i = b0 + lane;
         const int r = i < sr ? rows[q0 + i] : 0;
@@ -718,7 +1124,22 @@ __device__ __noinline__ int factor_block(const Walker& w, const Params& P, Share
     double nnz = 0.0;
     for (int r = threadIdx.x; r < w.n; r += 32) w.lev_u[r] = 0;
     const long long ti = clock64();
-    const int fl = P.ilu64 ? ilutp_warp<double>(w, P, sh, &npiv, &nnz, &p) : ilutp_warp<T>(w, P, sh, &npiv, &nnz, &p);
+    int fl;
+    const IluSm pl64 = ilu_sm_plan<double>(w.n, (size_t)P.dsm_bytes);
+    const IluSm plT = ilu_sm_plan<T>(w.n, (size_t)P.dsm_bytes);
+    // the shared-memory variant where the dense working row does not fit in shared memory
+    // (about n > 6000 with one walker CTA per SM); below that the dense row is in shared
+    // memory too and, with its U-row cache, the faster of the two
+    const bool dense_row_in_smem = 4 * (size_t)(pad4((w.n + 31) >> 5) + pad4((((w.n + 31) >> 5) + 31) >> 5)) +
+                                       16 + (size_t)16 * w.n <= (size_t)P.dsm_bytes;
+    if (P.ilu_variant == 0 && !dense_row_in_smem && w.u_head != nullptr && (P.ilu64 ? pl64.ok : plT.ok))
+      fl = P.ilu64 ? ilutp_warp_hash<double>(w, P, sh, pl64, &npiv, &nnz, &p)
+                   : ilutp_warp_hash<T>(w, P, sh, plT, &npiv, &nnz, &p);
+    else if (P.ilu_variant == 2 && w.u_head != nullptr && (P.ilu64 ? pl64.ok : plT.ok))  // forced (tests)
+      fl = P.ilu64 ? ilutp_warp_hash<double>(w, P, sh, pl64, &npiv, &nnz, &p)
+                   : ilutp_warp_hash<T>(w, P, sh, plT, &npiv, &nnz, &p);
+    else
+      fl = P.ilu64 ? ilutp_warp<double>(w, P, sh, &npiv, &nnz, &p) : ilutp_warp<T>(w, P, sh, &npiv, &nnz, &p);
     if (threadIdx.x == 0) w.ctl->cyc[PH_ILUTP] += clock64() - ti;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // scratch is reused by bulk copies
     if (threadIdx.x == 0) {
@@ -731,6 +1152,7 @@ __device__ __noinline__ int factor_block(const Walker& w, const Params& P, Share
       c->n_upd = 0;
       c->upd_nnz = 0;
       c->last_breakdown = fl & 1;
+      c->fresh = reorder ? 1 : 0;  // a synchronous reorder + refactorisation of the current matrix
       c->af_epoch += 1;  // a background factorisation requested before this one is stale
     }
   }

@@ -45,7 +45,8 @@ class vmc_solver_params(C.Structure):
                 ("max_updates", C.c_int), ("precision", C.c_int), ("engine", C.c_int),
                 ("block_threads", C.c_int), ("sm_refresh", C.c_int), ("refactor_lag", C.c_int),
                 ("refactor_reorder", C.c_int), ("trisolve", C.c_int),
-                ("graphs", C.c_int)]
+                ("graphs", C.c_int), ("trigger_rtol", C.c_double), ("trigger_its", C.c_int), ("sweep_moves", C.c_int),
+                ("ilutp_variant", C.c_int), ("trisolve_warp_rows", C.c_int)]
 
 
 class vmc_stats(C.Structure):
@@ -60,7 +61,8 @@ class vmc_stats(C.Structure):
                 ("ilu_rows", C.c_int64), ("ilu_elims", C.c_int64), ("ilu_cand", C.c_int64),
                 ("chunks_L", C.c_int), ("chunks_U", C.c_int), ("refactors_async", C.c_int64),
                 ("async_wait_cycles", C.c_int64), ("async_factor_cycles", C.c_int64), ("factor_set", C.c_int),
-                ("async_lag", C.c_int), ("max_updates", C.c_int)]
+                ("async_lag", C.c_int), ("max_updates", C.c_int), ("trigger_iterations", C.c_int64),
+                ("reorders_skipped", C.c_int64)]
 
 
 class vmc_tune_trial(C.Structure):
@@ -75,6 +77,7 @@ _SIG = {
     "vmc_destroy": (C.c_int, [C.c_void_p]),
     "vmc_init_positions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double]),
     "vmc_set_positions": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "vmc_set_positions_all": (C.c_int, [C.c_void_p, C.c_void_p]),
     "vmc_get_positions": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "vmc_walker_n": (C.c_int, [C.c_void_p, C.c_int]),
     "vmc_ratio": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
@@ -180,6 +183,14 @@ def vmc_walker_n(ctx, walker: int) -> int:
 def vmc_set_positions(ctx, walker: int, xyz) -> None:
     x = np.ascontiguousarray(xyz, dtype=np.float64)
     _check(lib().vmc_set_positions(ctx, walker, _p(x)), ctx)
+
+
+def vmc_set_positions_all(ctx, xyz) -> None:
+    """xyz: every walker's positions, walker-major (a list of (n_w, 3) arrays or one flat array)."""
+    if isinstance(xyz, (list, tuple)):
+        xyz = np.concatenate([np.asarray(x, dtype=np.float64).reshape(-1) for x in xyz])
+    x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
+    _check(lib().vmc_set_positions_all(ctx, _p(x)), ctx)
 
 
 def vmc_get_positions(ctx, walker: int) -> np.ndarray:
@@ -308,8 +319,23 @@ def vmc_philox_device(ctr, key) -> np.ndarray:
 
 def vmc_ratio_noalloc(system, params, xyz_dev, k: int, r_new, ratio_dev, stream=None) -> None:
     """Ratio of one move without device allocation; xyz_dev and ratio_dev are CUDA
-    tensors (float64, n*3 and 1 element) owned by the caller."""
+    tensors (float64, contiguous, n*3 and 1 element, on the current device) owned by
+    the caller.  stream: defaults to the current torch stream of xyz_dev's device, so
+    that the call is ordered after the work that produced the positions."""
+    import torch
+
     K, lat, a, kap, rc = system
+    n = int(K) ** 3 * (2 if int(lat) == 1 else 1)
+    cur = torch.cuda.current_device()
+    for name, t, need in (("xyz_dev", xyz_dev, 3 * n), ("ratio_dev", ratio_dev, 1)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise VmcError(1, f"{name} must be a contiguous float64 CUDA tensor")
+        if t.device.index != cur:
+            raise VmcError(1, f"{name} is on cuda:{t.device.index}, the current device is cuda:{cur}")
+        if t.numel() < need:
+            raise VmcError(1, f"{name} holds {t.numel()} doubles, {need} needed")
+    if stream is None:
+        stream = torch.cuda.current_stream(xyz_dev.device)
     sysc = vmc_system(int(K), int(lat), float(a), float(kap), float(rc))
     r = np.ascontiguousarray(r_new, dtype=np.float64)
     st = lib().vmc_ratio_noalloc(C.byref(sysc), C.byref(params) if params is not None else None, _p(xyz_dev), k,

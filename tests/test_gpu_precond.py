@@ -126,3 +126,37 @@ def test_reordering_matches_oracle_greedy_rule(vmc, K, jitter):
     partner = np.empty(K ** 3, dtype=np.int64)
     partner[Q] = P                         # orbital -> particle
     assert np.array_equal(por, partner[ooc])
+
+
+@pytest.fixture(scope="module")
+def hard_positions():
+    """n = 1000 positions after 20 Sherman-Morrison sweeps (hard, pivoting matrices)."""
+    s = O.system(10, 0, 1.0, 2.0, 1.5)
+    R0 = O.initial_positions(s, 3, 0.1)
+    return O.chain(s, 3, 0.2, R0, 20, solver=O.SOLVER_SHERMAN_MORRISON)[0]
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_shared_memory_ilutp_gives_the_dense_row_factors(vmc, hard_positions, prec):
+    """The shared-memory ILUTP (hashed working row) performs the elimination, drop, lfil
+    and pivot steps of the dense-working-row variant in the same order: the factors, the
+    permutation and a partial sweep's logs agree bit for bit."""
+    R = hard_positions
+    out = []
+    for variant in (2, 1):
+        ctx = vmc.vmc_create([(10, 0, 1.0, 2.0, 1.5)], vmc.params(precision=prec, ilutp_variant=variant,
+                                                                 sweep_moves=200))
+        try:
+            vmc.vmc_set_positions(ctx, 0, R)
+            L, U, perm = vmc.vmc_get_factors(ctx, 0)
+            st = vmc.vmc_get_stats(ctx, 0)
+            vmc.vmc_set_sweep_count(ctx, 20)
+            acc, rat = vmc.vmc_sweep(ctx, 1, 0.2, [3])
+            out.append((L, U, perm, st["pivots"], acc[:200].copy(), rat[:200].copy()))
+        finally:
+            vmc.vmc_destroy(ctx)
+    (L0, U0, p0, v0, a0, r0), (L1, U1, p1, v1, a1, r1) = out
+    assert np.array_equal(p0, p1) and v0 == v1
+    assert np.array_equal(L0.view(np.uint64), L1.view(np.uint64))
+    assert np.array_equal(U0.view(np.uint64), U1.view(np.uint64))
+    assert np.array_equal(a0, a1) and np.array_equal(r0.view(np.uint64), r1.view(np.uint64))

@@ -45,13 +45,31 @@ def test_noalloc_ratio_matches_context_ratio_twice(env, prec):
         ref = [vmc.vmc_ratio(ctx, 0, k, r) for k, r in moves]
     finally:
         vmc.vmc_destroy(ctx)
+    # the plain definition: dense LU solve of A z = e_k, ratio 1 + u^T z (Sec. 3 Eq. 13)
+    Z = O.sites(s)
+    A = O.slater_dense(s, Z, R)
+    exact = [O.ratio_dense(A, k, O.row_dense(s, Z, r))[0] for k, r in moves]
     xyz = torch.tensor(R.reshape(-1), dtype=torch.float64, device="cuda")
     out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
-    for (k, r), want in zip(moves, ref):
+    for (k, r), want, ex in zip(moves, ref, exact):
         out.fill_(float("nan"))
         vmc.vmc_ratio_noalloc(system, params, xyz, k, r, out)
         got = float(out.item())
         assert abs(got - want) <= max(RTOL * abs(want), ATOL), (k, got, want)
+        assert abs(got - ex) <= max(RTOL * abs(ex), ATOL), (k, got, ex)
+
+
+def test_noalloc_wrapper_checks_its_buffers(env):
+    vmc, torch = env
+    system = (6, 0, 1.0, 2.0, 1.5)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for bad in (torch.zeros(3 * 216 - 1, dtype=torch.float64, device="cuda"),   # too short
+                torch.zeros(3 * 216, dtype=torch.float32, device="cuda"),        # wrong dtype
+                torch.zeros(3 * 216 * 2, dtype=torch.float64, device="cuda")[::2],  # not contiguous
+                torch.zeros(3 * 216, dtype=torch.float64)):                      # host memory
+        with pytest.raises(vmc.VmcError) as e:
+            vmc.vmc_ratio_noalloc(system, None, bad, 0, [0.1, 0.1, 0.1], out)
+        assert e.value.status == 1
 
 
 def test_noalloc_rejects_systems_beyond_its_scratch(env):
