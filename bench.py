@@ -10,14 +10,17 @@ Stationary timed step.  The first sweeps of a chain are a transient: the electro
 leave their start positions and the Slater matrices grow harder to solve (the paper
 discards 20 sweeps, Sec. 4).  So the walkers are first taken through S = 20 sweeps
 by the engine's dense Sherman-Morrison path (FP64, untimed; the same Markov chain);
-their positions and the sweep counter S are the saved state.  Every bench step --
-warm-up and timed -- restores that state (vmc_set_positions_all: rows, reordering and
-a fresh ILUTP per walker; vmc_set_sweep_count(S)), outside the timed region, and then
-times the first 250 moves of sweep S of every walker (particles 0..249, a quarter
-sweep): 64 x 250 determinant ratios through the whole hot path (proposal, Slater row,
-ILUTP-preconditioned GMRES solve with refinement, stability monitor/reorder/refactor,
-Metropolis test, row commit and preconditioner update, background refactorisations).
-Every step is the same piece of work.
+their positions and the sweep counter S are the saved state.  The solver layout (CTA
+mapping, chain length, ILUTP fill limit) is then picked by the engine's autotuner with
+trials from that state.  Every bench step -- warm-up and timed -- restores the state
+(vmc_set_positions_all: rows, reordering and a fresh ILUTP per walker;
+vmc_set_sweep_count(S)), outside the timed region, and then times one budgeted advance
+of the batch by 64 x 250 moves: the walkers claim moves one at a time and each makes them
+along its own chain from particle 0 of sweep S, so that the SMs of walkers with cheaper
+solves do not idle while the slowest walker finishes.  Every move goes through the whole
+hot path (proposal, Slater row, ILUTP-preconditioned GMRES solve with refinement,
+stability monitor/reorder/refactor, Metropolis test, row commit and preconditioner
+update, background refactorisations).  Every step is the same amount of work.
 
 Reported beside the headline: the end-to-end rate through the host API, the same
 sweep in mixed precision, the dense Sherman-Morrison reference point, the plain FP64
@@ -252,6 +255,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-kernels", action="store_true")
     ap.add_argument("--headline-only", action="store_true", help="skip every leg after the headline")
+    ap.add_argument("--no-autotune", action="store_true", help="fixed solver layout instead of the autotuner's")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -300,17 +304,48 @@ def main():
     vmc.vmc_destroy(ctxd)
     log(f"equilibration: {EQUIL_SWEEPS} dense sweeps of {NW} walkers in {time.perf_counter() - t0:.1f} s")
 
-    def make(prec, engine, nw=NW):
-        return vmc.vmc_create(systems[:nw], vmc.params(precision=prec, engine=engine, sweep_moves=args.moves),
-                              stream=stream)
-
     def restore(ctx, nw=NW):
         vmc.vmc_set_positions_all(ctx, state[:nw * N * 3])
         vmc.vmc_set_sweep_count(ctx, EQUIL_SWEEPS)
 
-    def stationary_sweeps(ctx, steps, warmup, nw=NW):
-        """warmup + steps times: restore (untimed), flush L2, time sweep S on the stream.
-        Returns per-step ms and the statistics summed over the timed steps."""
+    # ---- solver layout: the autotuner's pick, from the saved state ---------------------
+    def tuned(prec):
+        base = vmc.params(precision=prec)
+        if args.no_autotune:
+            base.lfil_extra = 32 if prec == vmc.PREC_FP64 else 64
+            return base, []
+        t1 = time.perf_counter()
+        p, trials = vmc.vmc_autotune(systems, base, seeds, JITTER, SIGMA, 64, stream=stream, xyz=state,
+                                     sweep0=EQUIL_SWEEPS)
+        log(f"autotune (precision {prec}): {len(trials)} trials in {time.perf_counter() - t1:.1f} s; picked engine "
+            f"{p.engine}, {p.block_threads} threads, chain {p.max_updates}, lag {p.refactor_lag}, lfil {p.lfil_extra}")
+        return p, trials
+
+    def with_(p, **kw):
+        q = vmc.vmc_solver_params.from_buffer_copy(p)
+        for k, v in kw.items():
+            setattr(q, k, v)
+        return q
+
+    def summed(acc, st):
+        if acc is None:
+            return st
+        for a, b in zip(acc, st):
+            for key, v in b.items():
+                if isinstance(v, list):
+                    a[key] = [x + y for x, y in zip(a[key], v)]
+                elif key not in ("status", "factor_set", "async_lag", "max_updates", "n_updates", "levels_L",
+                                 "levels_U", "groups_L", "groups_U", "nnz_A", "nnz_LU", "pivots", "chunks_L",
+                                 "chunks_U", "N_max_seen"):
+                    a[key] += v
+                elif key == "N_max_seen":
+                    a[key] = max(a[key], v)
+        return acc
+
+    def stationary_steps(ctx, steps, warmup, nw=NW, advance=True):
+        """warmup + steps times: restore (untimed), flush L2, then time on the stream one
+        step: the budgeted advance of nw x moves moves (or, advance = False, one fixed
+        sweep).  Returns per-step ms and the statistics summed over the timed steps."""
         ms, acc = [], None
         for k in range(warmup + steps):
             restore(ctx, nw)
@@ -320,79 +355,72 @@ def main():
                 torch.distributed.barrier()
             torch.cuda.synchronize()
             e0.record(stream)
-            vmc.vmc_sweep_async(ctx, 1, SIGMA, seeds_dev[:nw])
+            if advance:
+                vmc.vmc_advance_async(ctx, nw * moves, SIGMA, seeds_dev[:nw])
+            else:
+                vmc.vmc_sweep_async(ctx, 1, SIGMA, seeds_dev[:nw])
             e1.record(stream)
             torch.cuda.synchronize()
             vmc.vmc_synchronize(ctx)
             if k >= warmup:
                 ms.append(e0.elapsed_time(e1))
-                st = [vmc.vmc_get_stats(ctx, w) for w in range(nw)]
-                if acc is None:
-                    acc = st
-                else:
-                    for a, b in zip(acc, st):
-                        for key, v in b.items():
-                            if isinstance(v, list):
-                                a[key] = [x + y for x, y in zip(a[key], v)]
-                            elif key not in ("status", "factor_set", "async_lag", "max_updates", "n_updates",
-                                             "levels_L", "levels_U", "nnz_A", "nnz_LU", "pivots", "chunks_L",
-                                             "chunks_U", "N_max_seen"):
-                                a[key] += v
-                            elif key == "N_max_seen":
-                                a[key] = max(a[key], v)
+                acc = summed(acc, [vmc.vmc_get_stats(ctx, w) for w in range(nw)])
         return ms, acc
 
-    # ---- headline: batched FP64, persistent engine (one launch per sweep) ---------------
+    p64, trials64 = tuned(vmc.PREC_FP64)
+    # ---- headline: batched FP64, persistent engine, budgeted advance -------------------
     t0 = time.perf_counter()
-    ctx = make(vmc.PREC_FP64, vmc.ENGINE_PERSISTENT)
+    ctx = vmc.vmc_create(systems, p64, stream=stream)
     lag = vmc.vmc_get_stats(ctx, 0)["async_lag"]
     refactoring = (f"background: a factor CTA per walker (cluster of 2) refactors a snapshot, adopted {lag} "
                    f"accepts later" if lag > 0 else "in line, when the update chain is full")
     kernel_name = "k_sweep_pair" if lag > 0 else "k_sweep"
     with Clocks(dev) as clk:
-        per_ms, stats = stationary_sweeps(ctx, args.steps, args.warmup)
+        per_ms, stats = stationary_steps(ctx, args.steps, args.warmup)
     total_ms = sum(per_ms)
     ratios_local = sum(s["proposals"] for s in stats)
     assert ratios_local == args.steps * NW * moves, (ratios_local, args.steps)
     ratios_all, t_max = replicas.reduce_run(ratios_local, total_ms)
     value = replicas.throughput(ratios_all, t_max / 1000.0)
     alg_bytes = sum(s["alg_bytes"] for s in stats)
-    log(f"headline: {args.warmup}+{args.steps} sweeps in {time.perf_counter() - t0:.1f} s; "
+    log(f"headline: {args.warmup}+{args.steps} steps in {time.perf_counter() - t0:.1f} s; "
         f"{value:.0f} ratios/s; per step ms {[round(x) for x in per_ms]}")
-    # ---- e2e: public host API (host seeds in, accept and ratio logs out, every step), the
-    #      same restored sweeps on the same context -----------------------------------------
+    # ---- e2e: public host API (host seeds in, accept counts out, every step), the same
+    #      restored steps on the same context ---------------------------------------------
     t0 = time.perf_counter()
     host_seeds = torch.tensor(seeds, dtype=torch.int64)        # the seeds' uint64 bytes (all positive)
-    acc_log = torch.zeros(NW * N, dtype=torch.uint8)
-    rat_log = torch.zeros(NW * N, dtype=torch.float64)
+    acc_out = torch.zeros(NW, dtype=torch.int64)
     try:
-        host_seeds, acc_log, rat_log = host_seeds.pin_memory(), acc_log.pin_memory(), rat_log.pin_memory()
+        host_seeds, acc_out = host_seeds.pin_memory(), acc_out.pin_memory()
         host_memory = "pinned"
     except RuntimeError:
         host_memory = "pageable"
     lib = vmc.lib()
     e2e_s = 0.0
-    for k in range(args.steps + 1):   # the first call sizes the context's log buffers: untimed
+    for k in range(args.steps):
         restore(ctx)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        st_ = lib.vmc_sweep(ctx, 1, SIGMA, vmc._p(host_seeds), vmc._p(acc_log), vmc._p(rat_log))
-        if k > 0:
-            e2e_s += time.perf_counter() - t1
+        st_ = lib.vmc_advance(ctx, NW * moves, SIGMA, vmc._p(host_seeds), vmc._p(acc_out))
+        e2e_s += time.perf_counter() - t1
         assert st_ == 0, vmc.vmc_last_error(ctx)
     e2e_count, e2e_s = replicas.reduce_run(args.steps * NW * moves, e2e_s)
     e2e_value = replicas.throughput(e2e_count, e2e_s)
     vmc.vmc_destroy(ctx)
-    log(f"e2e: {args.steps} sweeps in {time.perf_counter() - t0:.1f} s; {e2e_value:.0f} ratios/s")
+    log(f"e2e: {args.steps} steps in {time.perf_counter() - t0:.1f} s; {e2e_value:.0f} ratios/s")
 
     extra, skipped = {}, []
     side_steps = max(1, min(args.steps, 3))   # fixed-size side legs: at most 3 timed + 1 warm-up
     if rank == 0 and not args.headline_only:
-        # ---- mixed precision, same restored sweep ----------------------------------------
+        # ---- mixed precision, same restored steps ----------------------------------------
         if not over_budget():
             t0 = time.perf_counter()
-            ctxm = make(vmc.PREC_MIXED, vmc.ENGINE_PERSISTENT)
-            ms_m, sm = stationary_sweeps(ctxm, side_steps, 1)
+            pm, trials_m = tuned(vmc.PREC_MIXED)
+            extra["mixed_params"] = {"engine": pm.engine, "block_threads": pm.block_threads,
+                                     "max_updates": pm.max_updates, "refactor_lag": pm.refactor_lag,
+                                     "lfil_extra": pm.lfil_extra}
+            ctxm = vmc.vmc_create(systems, pm, stream=stream)
+            ms_m, sm = stationary_steps(ctxm, side_steps, 1)
             extra["mixed_value"] = sum(s["proposals"] for s in sm) / (sum(ms_m) / 1000.0)
             extra["mixed_inner_its_per_ratio"] = sum(s["inner_iterations"] for s in sm) / sum(s["proposals"] for s in sm)
             vmc.vmc_destroy(ctxm)
@@ -403,8 +431,9 @@ def main():
         #      same restored sweep, a fresh inverse at the restore --------------------------
         if not over_budget():
             t0 = time.perf_counter()
-            ctxd = make(vmc.PREC_FP64, vmc.ENGINE_DENSE_SM)
-            ms_d, sd_ = stationary_sweeps(ctxd, side_steps, 1)
+            ctxd = vmc.vmc_create(systems, vmc.params(precision=vmc.PREC_FP64, engine=vmc.ENGINE_DENSE_SM),
+                                  stream=stream)
+            ms_d, sd_ = stationary_steps(ctxd, side_steps, 1, advance=False)  # one full sweep a step
             extra["dense_sm_fp64_value"] = sum(x["proposals"] for x in sd_) / (sum(ms_d) / 1000.0)
             vmc.vmc_destroy(ctxd)
             log(f"dense: {time.perf_counter() - t0:.1f} s; {extra['dense_sm_fp64_value']:.0f} ratios/s")
@@ -413,13 +442,15 @@ def main():
         # ---- plain FP64 one-walker-per-launch path: walker 0's sweep S from the same state --
         if not args.no_plain and not over_budget():
             t0 = time.perf_counter()
-            ctxp = make(vmc.PREC_FP64, vmc.ENGINE_PLAIN, nw=1)
-            ms_p, sp_ = stationary_sweeps(ctxp, 1, 1, nw=1)
+            ctxp = vmc.vmc_create(systems[:1], with_(p64, engine=vmc.ENGINE_PLAIN, sweep_moves=moves),
+                                  stream=stream)
+            ms_p, sp_ = stationary_steps(ctxp, 1, 1, nw=1, advance=False)
             plain = sp_[0]["proposals"] / (ms_p[0] / 1000.0)
             vmc.vmc_destroy(ctxp)
             extra["plain_fp64_value"] = plain
-            extra["plain_fp64_sample"] = (f"walker 0, sweep {EQUIL_SWEEPS} from the saved state, {moves} launches "
-                                          f"(one per move), graph-replayed")
+            extra["plain_fp64_sample"] = (f"walker 0, moves 0..{moves - 1} of sweep {EQUIL_SWEEPS} from the saved "
+                                          f"state, one launch per move (graph-replayed), the headline's FP64 "
+                                          f"solver parameters")
             extra["speedup_vs_plain"] = value / plain
             if "mixed_value" in extra:
                 extra["speedup_vs_plain_mixed"] = extra["mixed_value"] / plain
@@ -475,21 +506,24 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N, "walkers_per_gpu": NW, "moves_per_walker_per_step": moves,
-                   "step": f"moves 0..{moves - 1} of sweep {EQUIL_SWEEPS} of every walker, restored before every "
-                           f"step from the state after {EQUIL_SWEEPS} discarded sweeps (restore untimed)",
-                   "engine": "persistent (one launch per sweep)", "gmres_m": 30,
-                   "ilutp": "drop 1e-4, permtol 0.5", "inner_rtol": 1e-10, "trigger_rtol": 1e-6,
+        "config": {"workload": WORKLOAD, "n": N, "walkers_per_gpu": NW, "moves_per_step": NW * moves,
+                   "step": f"{NW * moves} moves of the batch ({moves} a walker on average), claimed by the walkers "
+                           f"one at a time (budgeted advance) from sweep {EQUIL_SWEEPS} of the state after "
+                           f"{EQUIL_SWEEPS} discarded sweeps, restored before every step (restore untimed)",
+                   "engine": f"persistent, {p64.block_threads} threads a walker CTA, chain {p64.max_updates}",
+                   "gmres_m": 30, "ilutp": f"drop 1e-4, permtol 0.5, lfil {p64.lfil_extra}",
+                   "solver_layout": "autotuned from the saved state" if trials64 else "fixed (no autotune)",
+                   "inner_rtol": 1e-10, "trigger_rtol": 1e-6,
                    "refactorisation": refactoring, "l2": "256 MB buffer written between timed steps",
-                   "side_legs": f"mixed and dense: {side_steps} timed + 1 warm-up restored sweeps; plain: one"},
+                   "side_legs": f"mixed: {side_steps} timed + 1 warm-up restored steps (its own autotuned "
+                                f"layout); dense: full restored sweeps; plain: one step of walker 0"},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": host_seeds.numel() * host_seeds.element_size(),
-                "d2h_bytes_per_step": acc_log.numel() * acc_log.element_size()
-                + rat_log.numel() * rat_log.element_size(),
+                "d2h_bytes_per_step": acc_out.numel() * acc_out.element_size(),
                 "host_memory": host_memory,
-                "api": "vmc_sweep (host seeds in, accept and ratio logs out); the restore is outside the timing"},
+                "api": "vmc_advance (host seeds in, per-walker accept counts out); the restore is outside the timing"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": profiled_traffic(f"{kernel_name}_sc10_n1000_fp64.md"),
                      "note": f"{kernel_name}, algorithmic bytes from the kernel's per-phase counter; peak "
@@ -507,6 +541,8 @@ def main():
     }
     if skipped:
         out["skipped_over_budget"] = skipped
+    out["autotune_fp64"] = [{k: t[k] for k in ("engine", "block_threads", "max_updates", "refactor_lag",
+                                                  "lfil_extra", "ratios_per_s")} for t in trials64]
     out.update(extra)
     if not args.no_cpu_baseline and world == 1 and not args.headline_only:  # host cores, N = 1 only
         try:

@@ -84,7 +84,9 @@ typedef struct {
   double permtol;      /* ILUTP column-pivot tolerance: swap when permtol|w_j| > |w_i| (0.5) */
   int lfil_extra;      /* extra entries kept per L and per U row; < 0: ceil(avg nnz/row / 2) (-1) */
   int gmres_m;         /* Krylov dimension per inner solve, <= 40 (30)                   */
-  int max_restarts;    /* extra refinement passes allowed after a failed solve (10)      */
+  int max_restarts;    /* GMRES cycles of a solve beyond the first two (10); a solve still short
+                          of its goal then reorders, refactors and solves again from scratch with
+                          four times as many cycles, and reports VMC_ERR_NOCONV if that fails */
   double inner_rtol;   /* inner GMRES relative tolerance; <= 0: 1e-10 FP64, 1e-5 mixed (0) */
   double ratio_tol;    /* goal: predicted relative ratio error (1e-12)                   */
   double N_max;        /* reorder + refactor when the stability monitor N exceeds it (100) */
@@ -141,6 +143,16 @@ typedef struct {
                           rows, <= 32, is solved by one warp alone, with no barrier among the
                           solving warps after it (the other warps meet it before the next larger
                           level); 0 = every level by all solving warps (0) */
+  int trisolve_group;  /* grouped triangular solves (a partitioned inverse of each factor): at
+                          every factorisation, consecutive levels are merged into groups of at
+                          most this many levels and each row of a group is expanded, by
+                          substitution of the group's earlier rows, into a row that reads only
+                          the input vector and the solution of earlier groups; the solve then
+                          synchronises once per group instead of once per level.  The same
+                          operator as level-by-level substitution in exact arithmetic.  A level
+                          whose expanded rows would exceed max(capacity + 4, min(2 capacity,
+                          160)) entries starts a new group.  0 or 1: level by level; ignored
+                          with trisolve = 1 (8) */
 } vmc_solver_params;
 
 /* Per-walker statistics (Sec. 4 Tables 2 and 3 analogues). */
@@ -180,6 +192,9 @@ typedef struct {
   int factor_set;            /* factor set in use (0 or 1)                                  */
   int async_lag;             /* the refactor_lag in effect (0: in-line refactorisation)     */
   int max_updates;           /* the max_updates in effect                                   */
+  int groups_L, groups_U;    /* synchronisation steps of the triangular solves at the last
+                                factorisation (groups of levels; = the level counts when the
+                                solves are not grouped)                                       */
   int64_t trigger_iterations; /* GMRES iterations until the residual reached trigger_rtol, summed
                                 over solves (the paper's iteration count k1 at its tolerance 1e-6) */
   int64_t reorders_skipped;  /* triggers (monitor, non-convergence, slow) that fired while the
@@ -199,24 +214,34 @@ typedef struct {
   int refactor_lag;    /* the lag in effect: > 0 background refactorisation (walker pairs) */
   double ratios_per_s; /* measured determinant ratios per second (0 when the trial failed) */
   int status;          /* vmc_status of the trial                                        */
+  int lfil_extra;      /* ILUTP fill limit of the trial (-1: half the average row count)   */
 } vmc_tune_trial;
 
-/* Autotuner: picks the launch mapping for these walkers by timing short trials on the
- * device.  Candidates: a CTA pair per walker with background refactorisation (when the
- * pairs fit), a CTA per walker (persistent), one launch per step (STEP engine); 128 or
- * 256 threads per CTA; then max_updates of 32, 64 or 128 for the best of those.  Each
- * trial creates a context from `params` with the candidate's fields, starts the walkers
- * from `seeds` and `jitter`, runs one untimed and one timed partial sweep of `steps`
- * moves per walker (proposal width sigma) and destroys the context.  The mapping does
- * not change the method -- only how it is laid out on the GPU, and the rounding.
- * params (in/out): the base parameters; on return engine, block_threads, max_updates and
- * refactor_lag hold the fastest trial's.  trials (nullable): receives up to max_trials
- * trial records, *n_trials (nullable) their number.  stream as in vmc_create.  Returns
- * VMC_ERR_INVALID on bad arguments or a DENSE_SM engine, the first failure if every trial
- * fails, else VMC_OK. */
+/* Autotuner: picks the launch mapping and solver layout for these walkers by timing
+ * short trials on the device.  Candidates: a CTA pair per walker with background
+ * refactorisation (when the pairs fit), a CTA per walker (persistent), one launch per
+ * step (STEP engine); 128 or 256 threads per CTA; then max_updates of 32, 64 or 128 for
+ * the best of those; then the ILUTP fill limit lfil_extra of -1 (half the average row
+ * count, the paper's), 16, 32 or 48 for the best of those.  Each trial creates a context
+ * from `params` with the candidate's fields, starts the walkers from `seeds` and
+ * `jitter`, runs one untimed and one timed partial sweep of `steps` moves per walker
+ * (proposal width sigma) and destroys the context.  The mapping and the fill limit do
+ * not change the method's results -- only its cost, and the rounding.
+ * params (in/out): the base parameters; on return engine, block_threads, max_updates,
+ * refactor_lag and lfil_extra hold the fastest trial's.  trials (nullable): receives up to
+ * max_trials trial records, *n_trials (nullable) their number.  stream as in vmc_create.
+ * Returns VMC_ERR_INVALID on bad arguments or a DENSE_SM engine, the first failure if
+ * every trial fails, else VMC_OK. */
 vmc_status vmc_autotune(const vmc_system* systems, int n_walkers, vmc_solver_params* params, const uint64_t* seeds,
                         double jitter, double sigma, int steps, vmc_tune_trial* trials, int max_trials,
                         int* n_trials, void* stream);
+/* vmc_autotune from a given state (e.g. an equilibrated one, where the solves are far
+ * harder than at the start): xyz (host, walker-major, as vmc_set_positions_all) and the
+ * sweep index sweep0; both the untimed and the timed trial sweep start from that state.
+ * xyz = NULL: as vmc_autotune (start from seeds and jitter). */
+vmc_status vmc_autotune_state(const vmc_system* systems, int n_walkers, vmc_solver_params* params,
+                              const uint64_t* seeds, double jitter, const double* xyz, int64_t sweep0, double sigma,
+                              int steps, vmc_tune_trial* trials, int max_trials, int* n_trials, void* stream);
 
 /* Create a context for n_walkers walkers; systems[w] is walker w's system
  * (walkers may differ in size: an uneven batch).  systems: host, n_walkers entries,
@@ -302,6 +327,27 @@ vmc_status vmc_sweep(vmc_ctx* ctx, int n_sweeps, double sigma, const uint64_t* s
  * sweep graph's state), VMC_ERR_CUDA. */
 vmc_status vmc_sweep_async(vmc_ctx* ctx, int n_sweeps, double sigma, const uint64_t* seeds_dev,
                            uint8_t* accept_log_dev, double* ratio_log_dev);
+/* Budgeted advance (PERSISTENT engine only): the batch makes total_moves Metropolis
+ * moves in all, claimed one at a time by the walkers, so that walkers whose solves are
+ * cheaper make more of them and no SM idles while the slowest walker finishes a fixed
+ * share (the walkers' solve costs differ several-fold).  Every walker continues its own
+ * chain from where it stands -- the particle after its last move, or particle 0 of the
+ * context's sweep counter after vmc_create / vmc_set_positions(_all) / vmc_sweep --
+ * through the particles in order and on into the following sweeps; its moves are the
+ * ones full sweeps make (the same proposals, uniforms and factor adoption points), only
+ * how many a walker makes in one call depends on timing.  The context's sweep counter is
+ * not advanced; vmc_sweep starts every walker at particle 0 of that counter again.  No
+ * logs.  seeds_dev: device, n_walkers seeds, valid until the work completes.  Enqueues
+ * only; failures surface at vmc_synchronize.  VMC_ERR_INVALID for another engine or bad
+ * arguments, VMC_ERR_STATE before positions are set. */
+vmc_status vmc_advance_async(vmc_ctx* ctx, int64_t total_moves, double sigma, const uint64_t* seeds_dev);
+/* vmc_advance_async with host seeds (copied), waiting for completion; accepts_out (host,
+ * n_walkers, nullable) receives every walker's accepted-move count (the statistic). */
+vmc_status vmc_advance(vmc_ctx* ctx, int64_t total_moves, double sigma, const uint64_t* seeds,
+                       int64_t* accepts_out);
+/* Where walker w's chain stands: the next move is particle *particle of sweep *sweep
+ * (host outputs; synchronises the stream).  VMC_ERR_INVALID for bad arguments. */
+vmc_status vmc_get_progress(vmc_ctx* ctx, int walker, int64_t* sweep, int* particle);
 /* Device status check after vmc_sweep_async: synchronises and returns the first
  * walker error. */
 vmc_status vmc_synchronize(vmc_ctx* ctx);

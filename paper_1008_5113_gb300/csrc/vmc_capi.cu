@@ -20,6 +20,10 @@ using namespace vmc;
 // ---------------------------------------------------------------------------
 namespace vmc {
 
+int expanded_row_cap(int capLU) {
+  return (std::max(capLU + 4, std::min(2 * capLU, 160)) + 3) / 4 * 4;
+}
+
 void plan_smem(int ybytes, int budget, Params& P, bool allow_sf) {
   int avail = budget;
   P.tri_sf = 0;
@@ -149,6 +153,7 @@ struct vmc_ctx {
   Ctl* dShadow = nullptr;
   int launch_seq = 0;
   double* d_energy = nullptr;  // kinetic energies, one per walker (in the arena)
+  unsigned long long* d_budget = nullptr;  // move counter of the budgeted advance (in the arena)
   // CUDA graph of one sweep of the STEP / PLAIN engines (replayed once per sweep)
   cudaGraphExec_t graph = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -216,6 +221,7 @@ extern "C" vmc_status vmc_default_params(vmc_solver_params* p) {
   p->sweep_moves = 0;
   p->ilutp_variant = 0;
   p->trisolve_warp_rows = 0;
+  p->trisolve_group = 8;
   return VMC_OK;
 }
 
@@ -337,6 +343,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   else if (p.sweep_moves < 0) st = bad("sweep_moves must be >= 0");
   else if (p.ilutp_variant < 0 || p.ilutp_variant > 2) st = bad("ilutp_variant must be 0, 1 or 2");
   else if (p.trisolve_warp_rows < 0 || p.trisolve_warp_rows > 32) st = bad("trisolve_warp_rows must be in [0, 32]");
+  else if (p.trisolve_group < 0 || p.trisolve_group > 64) st = bad("trisolve_group must be in [0, 64]");
   else if (!(p.trigger_rtol < 1.0)) st = bad("trigger_rtol must be below 1");
   if (st != VMC_OK) { *out = ctx; return st; }
   ctx->fp64 = p.precision == VMC_PREC_FP64;
@@ -356,6 +363,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   ctx->P.step_limit = p.sweep_moves;
   ctx->P.ilu_variant = p.ilutp_variant;
   ctx->P.warp_rows = p.trisolve_warp_rows;
+  ctx->P.tri_group = p.trisolve == 1 ? 1 : std::max(1, p.trisolve_group);  // the sync-free solves read levels
   {
     // background refactorisation (persistent engine) when asked for, or by default when
     // every walker pair fits and no system is larger than kAutoPairMaxN; the chain length
@@ -407,6 +415,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     const int n = L.n, cap = L.cap;
     const int pmax = p.lfil_extra >= 0 ? p.lfil_extra : (cap + 1) / 2;
     const int capLU = (cap + pmax + 2 + 3) / 4 * 4;  // rows of 16-byte multiples (bulk copies)
+    const int exmax = expanded_row_cap(capLU);
     auto& o = offs[w];
     o.push_back(cv.take<double>((size_t)n * 3));       // 0 Z
     o.push_back(cv.take<int>(n));                      // 1 col_of_orb
@@ -420,7 +429,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     o.push_back(cv.take<int>(n));                      // 9 a_len
     o.push_back(cv.take<int>((size_t)n * capLU));      // 10 l_col
     o.push_back(cv.take<double>((size_t)n * capLU));   // 11 l_val64
-    const size_t sbytes = (size_t)n * (256 + 12 * (size_t)capLU);
+    const size_t sbytes = (size_t)n * (256 + 12 * (size_t)std::max(capLU, exmax));
     o.push_back(cv.take<unsigned char>(sbytes));       // 12 lstream
     o.push_back(cv.take<int>(n));                      // 13 l_len
     o.push_back(cv.take<int>((size_t)n * capLU));      // 14 u_col
@@ -449,7 +458,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     o.push_back(cv.take<double>((size_t)kMaxUpd * kMaxUpd));  // 37 upd_G
     o.push_back(cv.take<char>((size_t)(m + 1) * n * Tsz));    // 38 V
     o.push_back(cv.take<char>((size_t)m * n * Tsz));          // 39 Zk
-    o.push_back(cv.take<char>((size_t)n * Tsz));              // 40 tv
+    o.push_back(cv.take<char>((size_t)3 * n * Tsz));          // 40 tv (three solve vectors)
     o.push_back(cv.take<double>(n));                   // 41 x64
     o.push_back(cv.take<double>(n));                   // 42 r64
     o.push_back(cv.take<int>(cap));                    // 43 pend_acol
@@ -496,6 +505,12 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     }
     o.push_back(cv.take<double2>(n));                  // u_head of factor set 0 (then of set 1)
     if (ctx->pair) o.push_back(cv.take<double2>(n));
+    for (int sset = 0; sset < (ctx->pair ? 2 : 1); ++sset) {  // expanded rows of each factor set
+      o.push_back(cv.take<int>(n));                      // ex_len
+      o.push_back(cv.take<int>((size_t)n * exmax));      // ex_col
+      o.push_back(cv.take<double>((size_t)n * exmax));   // ex_val
+      o.push_back(cv.take<int>(n + 1));                  // gptr
+    }
     Walker& W = ctx->hw[w];
     std::memset(&W, 0, sizeof(W));
     W.n = n; W.K = systems[w].K; W.lattice = systems[w].lattice; W.cap = cap; W.capLU = capLU;
@@ -520,7 +535,8 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
       *out = ctx;
       return fail(ctx, VMC_ERR_CUDA, "no usable CUDA device (shared-memory attributes unavailable)");
     }
-    const int ybytes = (int)(((size_t)ctx->max_n * Tsz + 127) / 128 * 128);
+    const int nvec = ctx->P.tri_group > 1 ? 3 : 1;  // grouped solves keep three vectors
+    const int ybytes = (int)(((size_t)nvec * ctx->max_n * Tsz + 127) / 128 * 128);
     const int budget1 = optin - stat;
     const int budget2 = per_sm / 2 - 1024 - stat;
     int budget = budget1;
@@ -531,6 +547,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   const size_t ctl_off = cv.take<Ctl>(n_walkers);
   const size_t walk_off = cv.take<Walker>(n_walkers);
   const size_t energy_off = cv.take<double>(n_walkers);
+  const size_t budget_off = cv.take<unsigned long long>(1);
   const size_t shadow_off = ctx->pair ? cv.take<Ctl>(n_walkers) : 0;
   const size_t walk1_off = ctx->pair ? cv.take<Walker>(n_walkers) : 0;
   const size_t walkf_off = ctx->pair ? cv.take<Walker>(2 * (size_t)n_walkers) : 0;
@@ -543,6 +560,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   ctx->dCtl = (Ctl*)(A + ctl_off);
   ctx->dW = (Walker*)(A + walk_off);
   ctx->d_energy = (double*)(A + energy_off);
+  ctx->d_budget = (unsigned long long*)(A + budget_off);
   for (int w = 0; w < n_walkers; ++w) {
     const auto& o = offs[w];
     Walker& W = ctx->hw[w];
@@ -598,6 +616,14 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     W.lvl_nchunk = (int*)(A + o[48]);
     W.seg_meta = (int4*)(A + o[49]);
     W.u_head = (double2*)(A + o[ctx->pair ? 82 : 50]);
+    {
+      const size_t e0 = ctx->pair ? 84 : 51;
+      W.exmax = expanded_row_cap(W.capLU);
+      W.ex_len = (int*)(A + o[e0]);
+      W.ex_col = (int*)(A + o[e0 + 1]);
+      W.ex_val = (double*)(A + o[e0 + 2]);
+      W.gptr = (int*)(A + o[e0 + 3]);
+    }
     W.ctl = ctx->dCtl + w;
     const Layout& L = lay[w];
     e = cudaMemcpyAsync((void*)W.Z, L.Z.data(), sizeof(double) * L.Z.size(), cudaMemcpyHostToDevice, ctx->stream);
@@ -645,6 +671,10 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
       W1.lvl_nchunk = (int*)(A + o[72]);
       W1.seg_meta = (int4*)(A + o[73]);
       W1.u_head = (double2*)(A + o[83]);
+      W1.ex_len = (int*)(A + o[88]);
+      W1.ex_col = (int*)(A + o[89]);
+      W1.ex_val = (double*)(A + o[90]);
+      W1.gptr = (int*)(A + o[91]);
       W0.snap_len = (int*)(A + o[74]);
       W0.snap_col = (int*)(A + o[75]);
       W0.snap_val = (double*)(A + o[76]);
@@ -976,6 +1006,53 @@ extern "C" vmc_status vmc_sweep_async(vmc_ctx* ctx, int n_sweeps, double sigma, 
   return enqueue_sweeps(ctx, n_sweeps, sigma, seeds_dev, accept_log_dev, ratio_log_dev);
 }
 
+extern "C" vmc_status vmc_advance_async(vmc_ctx* ctx, int64_t total_moves, double sigma, const uint64_t* seeds_dev) {
+  if (!ctx || !seeds_dev || total_moves < 0 || !(sigma >= 0.0)) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  if (ctx->prm.engine != VMC_ENGINE_PERSISTENT || ctx->dense)
+    return fail(ctx, VMC_ERR_INVALID, "the budgeted advance needs the persistent engine");
+  if (!ctx->ready) return fail(ctx, VMC_ERR_STATE, "positions not set");
+  for (int w = 0; w < ctx->nw; ++w) ctx->pending[w] = 0;
+  if (total_moves == 0) return VMC_OK;
+  CK(cudaMemsetAsync(ctx->d_budget, 0, sizeof(unsigned long long), ctx->stream), "budget counter");
+  Params P = ctx->P;
+  P.budget_ctr = ctx->d_budget;
+  P.budget_total = total_moves;
+  const LaunchCfg L = cfg(ctx);
+  if (ctx->pair) {
+    if (++ctx->launch_seq <= 0) ctx->launch_seq = 1;
+    CK(launch_sweep_pair(L, ctx->dW, 0, ctx->nw, P, 0, ctx->sweeps, sigma, seeds_dev, nullptr, nullptr,
+                         ctx->launch_seq), "advance kernel (walker pairs)");
+  } else {
+    CK(launch_sweep(L, ctx->dW, 0, ctx->nw, P, 0, ctx->sweeps, sigma, seeds_dev, nullptr, nullptr), "advance kernel");
+  }
+  return VMC_OK;
+}
+
+extern "C" vmc_status vmc_advance(vmc_ctx* ctx, int64_t total_moves, double sigma, const uint64_t* seeds,
+                                  int64_t* accepts_out) {
+  if (!ctx || !seeds) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  CK(cudaMemcpyAsync(ctx->d_seeds, seeds, sizeof(uint64_t) * ctx->nw, cudaMemcpyHostToDevice, ctx->stream), "seeds");
+  vmc_status st = vmc_advance_async(ctx, total_moves, sigma, ctx->d_seeds);
+  if (st != VMC_OK) return st;
+  st = check_walker_status(ctx);
+  if (st != VMC_OK || !accepts_out) return st;
+  std::vector<Ctl> h(ctx->nw);
+  CK(cudaMemcpyAsync(h.data(), ctx->dCtl, sizeof(Ctl) * ctx->nw, cudaMemcpyDeviceToHost, ctx->stream), "accepts");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  for (int w = 0; w < ctx->nw; ++w) accepts_out[w] = h[w].accepts;
+  return VMC_OK;
+}
+
+extern "C" vmc_status vmc_get_progress(vmc_ctx* ctx, int walker, int64_t* sweep, int* particle) {
+  if (!ctx || !sweep || !particle || walker < 0 || walker >= ctx->nw) return fail(ctx, VMC_ERR_INVALID, "bad arguments");
+  Ctl h;
+  CK(cudaMemcpyAsync(&h, ctx->dCtl + walker, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream), "progress");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  *sweep = h.pos_valid ? h.pos_sweep : ctx->sweeps;
+  *particle = h.pos_valid ? h.pos_k : 0;
+  return VMC_OK;
+}
+
 extern "C" vmc_status vmc_synchronize(vmc_ctx* ctx) {
   if (!ctx) return VMC_ERR_INVALID;
   return check_walker_status(ctx);
@@ -1025,6 +1102,8 @@ extern "C" vmc_status vmc_get_stats(vmc_ctx* ctx, int walker, vmc_stats* out) {
   out->max_updates = ctx->P.max_updates;
   out->reorders_skipped = h.reorder_skipped;
   out->trigger_iterations = h.trig_its;
+  out->groups_L = h.ngrp_l;
+  out->groups_U = h.ngrp_u;
   return VMC_OK;
 }
 
@@ -1188,13 +1267,25 @@ extern "C" vmc_status vmc_philox_device(const uint32_t* ctr, const uint32_t* key
 
 // ---- autotuner ---------------------------------------------------------------------
 static vmc_status tune_trial(const vmc_system* systems, int nw, const vmc_solver_params& p, const uint64_t* seeds,
-                             double jitter, double sigma, int steps, void* stream, double* rate, int* lag, int* mu) {
+                             double jitter, const double* xyz, int64_t sweep0, double sigma, int steps, void* stream,
+                             double* rate, int* lag, int* mu) {
   vmc_ctx* c = nullptr;
   *rate = 0.0;
   *lag = 0;
   *mu = p.max_updates;
   vmc_status st = vmc_create(systems, nw, &p, stream, &c);
-  if (st == VMC_OK) st = vmc_init_positions(c, seeds, jitter);
+  auto start = [&]() -> vmc_status {
+    if (!xyz) return vmc_init_positions(c, seeds, jitter);
+    vmc_status s2 = vmc_set_positions_all(c, xyz);
+    if (s2 == VMC_OK) s2 = vmc_set_sweep_count(c, sweep0);
+    return s2;
+  };
+  if (st == VMC_OK) {
+    if (cudaMemcpyAsync(c->d_seeds, seeds, sizeof(uint64_t) * nw, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+      st = VMC_ERR_CUDA;
+    else
+      st = start();
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (st == VMC_OK) {
     *lag = c->P.af_lag;
@@ -1204,6 +1295,7 @@ static vmc_status tune_trial(const vmc_system* systems, int nw, const vmc_solver
     for (int w = 0; w < nw; ++w) moves += std::min(c->hw[w].n, steps);
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = VMC_ERR_CUDA;
     if (st == VMC_OK) st = enqueue_sweeps(c, 1, sigma, c->d_seeds, nullptr, nullptr);  // untimed
+    if (st == VMC_OK && xyz) st = start();  // the timed sweep from the same state
     if (st == VMC_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = VMC_ERR_CUDA;
     if (st == VMC_OK) st = enqueue_sweeps(c, 1, sigma, c->d_seeds, nullptr, nullptr);  // timed
     if (st == VMC_OK && cudaEventRecord(e1, c->stream) != cudaSuccess) st = VMC_ERR_CUDA;
@@ -1217,14 +1309,15 @@ static vmc_status tune_trial(const vmc_system* systems, int nw, const vmc_solver
   return st;
 }
 
-extern "C" vmc_status vmc_autotune(const vmc_system* systems, int n_walkers, vmc_solver_params* params,
-                                   const uint64_t* seeds, double jitter, double sigma, int steps,
-                                   vmc_tune_trial* trials, int max_trials, int* n_trials, void* stream) {
+extern "C" vmc_status vmc_autotune_state(const vmc_system* systems, int n_walkers, vmc_solver_params* params,
+                                         const uint64_t* seeds, double jitter, const double* xyz, int64_t sweep0,
+                                         double sigma, int steps, vmc_tune_trial* trials, int max_trials,
+                                         int* n_trials, void* stream) {
   if (n_trials) *n_trials = 0;
   if (!systems || !params || !seeds || n_walkers <= 0 || steps <= 0 || !(sigma >= 0.0) || !(jitter >= 0.0) ||
-      (trials && max_trials < 0) || params->engine == VMC_ENGINE_DENSE_SM)
+      sweep0 < 0 || (trials && max_trials < 0) || params->engine == VMC_ENGINE_DENSE_SM)
     return VMC_ERR_INVALID;
-  struct Cand { int engine, threads, mu, lag; };
+  struct Cand { int engine, threads, mu, lag, lfil; };
   std::vector<vmc_tune_trial> done;
   vmc_status first_err = VMC_OK;
   auto run = [&](const Cand& cd) -> double {
@@ -1233,26 +1326,28 @@ extern "C" vmc_status vmc_autotune(const vmc_system* systems, int n_walkers, vmc
     p.block_threads = cd.threads;
     p.max_updates = cd.mu;
     p.refactor_lag = cd.lag;
+    p.lfil_extra = cd.lfil;
     double rate = 0.0;
     int lag = 0, mu = cd.mu;
-    const vmc_status st = tune_trial(systems, n_walkers, p, seeds, jitter, sigma, steps, stream, &rate, &lag, &mu);
+    const vmc_status st = tune_trial(systems, n_walkers, p, seeds, jitter, xyz, sweep0, sigma, steps, stream, &rate,
+                                     &lag, &mu);
     if (st != VMC_OK && first_err == VMC_OK) first_err = st;
-    vmc_tune_trial t{cd.engine, cd.threads, mu, lag, st == VMC_OK ? rate : 0.0, (int)st};
+    vmc_tune_trial t{cd.engine, cd.threads, mu, lag, st == VMC_OK ? rate : 0.0, (int)st, cd.lfil};
     done.push_back(t);
     return st == VMC_OK ? rate : 0.0;
   };
-  // phase 1: mapping x CTA size at the given chain length
-  const int mu0 = params->max_updates;
+  // phase 1: mapping x CTA size at the given chain length and fill limit
+  const int mu0 = params->max_updates, lf0 = params->lfil_extra;
   double best = -1.0;
-  Cand bc{VMC_ENGINE_PERSISTENT, 256, mu0, 0};
+  Cand bc{VMC_ENGINE_PERSISTENT, 256, mu0, 0, lf0};
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const bool pairs_fit = auto_pairs_fit(systems, n_walkers, nsm) && (mu0 < 0 || mu0 >= 2);  // refactor_lag = -1's rule
   for (int threads : {128, 256}) {
-    const Cand cands[3] = {{VMC_ENGINE_PERSISTENT, threads, mu0, -1},
-                           {VMC_ENGINE_PERSISTENT, threads, mu0, 0},
-                           {VMC_ENGINE_STEP, threads, mu0, 0}};
+    const Cand cands[3] = {{VMC_ENGINE_PERSISTENT, threads, mu0, -1, lf0},
+                           {VMC_ENGINE_PERSISTENT, threads, mu0, 0, lf0},
+                           {VMC_ENGINE_STEP, threads, mu0, 0, lf0}};
     for (const Cand& cd : cands) {
       if (cd.lag == -1 && !pairs_fit) continue;  // would be the same as the next candidate
       const double r = run(cd);
@@ -1269,6 +1364,15 @@ extern "C" vmc_status vmc_autotune(const vmc_system* systems, int n_walkers, vmc
     const double r = run(cd);
     if (r > best) { best = r; bc = cd; bc.lag = done.back().refactor_lag; }
   }
+  // phase 3: ILUTP fill limit for the best mapping and chain length
+  for (int lf : {-1, 16, 32, 48}) {
+    if (lf == bc.lfil) continue;
+    Cand cd = bc;
+    cd.lfil = lf;
+    if (bc.lag > 0) cd.lag = -1;
+    const double r = run(cd);
+    if (r > best) { best = r; bc = cd; bc.lag = done.back().refactor_lag; }
+  }
   if (trials)
     for (int i = 0; i < (int)done.size() && i < max_trials; ++i) trials[i] = done[i];
   if (n_trials) *n_trials = (int)done.size();
@@ -1277,5 +1381,13 @@ extern "C" vmc_status vmc_autotune(const vmc_system* systems, int n_walkers, vmc
   params->block_threads = bc.threads;
   params->max_updates = bc.mu;
   params->refactor_lag = bc.lag;
+  params->lfil_extra = bc.lfil;
   return VMC_OK;
+}
+
+extern "C" vmc_status vmc_autotune(const vmc_system* systems, int n_walkers, vmc_solver_params* params,
+                                   const uint64_t* seeds, double jitter, double sigma, int steps,
+                                   vmc_tune_trial* trials, int max_trials, int* n_trials, void* stream) {
+  return vmc_autotune_state(systems, n_walkers, params, seeds, jitter, nullptr, 0, sigma, steps, trials, max_trials,
+                            n_trials, stream);
 }

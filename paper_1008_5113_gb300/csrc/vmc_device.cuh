@@ -56,6 +56,7 @@ struct Ctl {
   int last_pivots;
   int last_breakdown;
   int nchunk_l, nchunk_u;
+  int ngrp_l, ngrp_u;  // barriers of the triangular solves (groups; = levels when not grouped)
   double pend_r[3];
   double pend_ratio;
   double pend_grad[3], pend_lap;  // gradient / Laplacian at the pending position (when asked)
@@ -89,6 +90,10 @@ struct Ctl {
   int fresh;
   long long reorder_skipped;
   long long trig_its;  // iterations until the residual reached trig_rtol, summed over solves
+  // position of the walker's chain after a budgeted advance: the next move is particle
+  // pos_k of sweep pos_sweep (pos_valid = 0: particle 0 of the context's sweep counter)
+  long long pos_sweep;
+  int pos_k, pos_valid;
 };
 
 // Immutable-per-context description of one walker: sizes and device pointers.
@@ -107,7 +112,9 @@ struct Walker {
   int* l_col; double* l_val64; int* l_len;
   int* u_col; double* u_val64; int* u_len;
   double* u_dinv64;
-  double2* u_head;        // per U row {1 / u_rr, length}, written by the shared-memory ILUTP (16 B: one bulk copy)
+  double2* u_head;        // per U row {1 / u_rr, length}, written by the shared-memory ILUTP
+  // grouped triangular solves: expanded rows (exmax entries each) and group row pointers
+  int exmax; int* ex_len; int* ex_col; double* ex_val; int* gptr;
   // level-ordered chunk streams of L and U for the staged triangular solves
   unsigned char* lstream; unsigned char* ustream;
   int2* lchunk; int2* uchunk;   // per chunk {byte offset, bytes}
@@ -161,6 +168,11 @@ struct Params {
   int trig_its;     // ... within this many GMRES iterations (all cycles)
   int ilu_variant;  // 0: auto (hash working row where the dense one misses shared memory); 1: dense; 2: hash
   int warp_rows;    // levels of at most this many rows: triangular-solve rows by one warp, no barrier
+  int tri_group;    // > 1: grouped triangular solves, at most this many levels per group
+  // budgeted advance of the persistent engine: the walkers claim moves one at a time from
+  // *budget_ctr until budget_total are claimed (nullptr: fixed sweeps)
+  unsigned long long* budget_ctr;
+  long long budget_total;
 };
 
 // Shared memory of a walker CTA (static, < 48 KB).
@@ -196,6 +208,19 @@ struct __align__(16) Shared {
   int iflag[12];
   double dflag[8];
 };
+
+// Grouped triangular solves (expand_groups): on when asked for, the walker has the
+// scratch for the expanded rows, and one warp-sized hash accumulator per warp of the
+// CTA fits the dynamic shared memory.  Decided the same way at factorisation and solve.
+__device__ __forceinline__ int group_hash_slots(int exmax) {
+  int hs = 64;
+  while (hs < 2 * exmax) hs <<= 1;
+  return hs;
+}
+__device__ __forceinline__ bool grouped_solves(const Walker& w, const Params& P) {
+  return P.tri_group > 1 && w.ex_col != nullptr &&
+         (size_t)(blockDim.x >> 5) * 12u * (size_t)group_hash_slots(w.exmax) <= (size_t)P.dsm_bytes;
+}
 
 // ---- dynamic shared memory, mbarriers and bulk (TMA) copies ----------------
 __device__ __forceinline__ unsigned char* dyn_smem() {

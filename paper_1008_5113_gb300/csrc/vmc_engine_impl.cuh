@@ -58,7 +58,7 @@ __device__ __noinline__ void solve_with_controller(const Walker& w, const Params
     const int brow2 = w.row_of_part[k];
     t0 = clock64();
     solve_first<T>(w, P, brow2, rtol, o, sh);
-    refine<T>(w, P, brow2, rtol, 2 + P.max_restarts, o, sh);
+    refine<T>(w, P, brow2, rtol, 4 * (2 + P.max_restarts), o, sh);  // and allow more cycles
     if (threadIdx.x == 0) c->cyc[PH_REFINE] += clock64() - t0;
   }
   const int kits = o.its_trig >= 0 ? o.its_trig : o.total_its;  // iterations to the tolerance
@@ -282,6 +282,7 @@ __device__ void af_swap(const Walker& w0, const Params& P, Shared& sh) {
     c->upd_nnz = nnzu;
     c->n_upd = len;
     c->nlev_l = sc->nlev_l; c->nlev_u = sc->nlev_u;
+    c->ngrp_l = sc->ngrp_l; c->ngrp_u = sc->ngrp_u;
     c->nchunk_l = sc->nchunk_l; c->nchunk_u = sc->nchunk_u;
     c->nnz_LU = sc->nnz_LU; c->nnz_A = sc->nnz_A;
     c->p_lfil = sc->p_lfil; c->last_pivots = sc->last_pivots; c->last_breakdown = 0;
@@ -415,6 +416,35 @@ __device__ __noinline__ void af_factor_loop(const Walker& w0, const Params& P, i
   }
 }
 
+// Budgeted advance (block-wide): the walker claims moves one at a time from the batch's
+// budget and makes them along its own chain -- particle pos_k of sweep pos_sweep onwards
+// -- so that walkers whose solves are cheaper make more moves and no SM idles while the
+// slowest walker finishes a fixed share.  Each walker's chain is the one fixed sweeps
+// give (the proposals and uniforms are keyed by sweep and particle, and the factor
+// adoption points by accept counts); only the number of moves each walker makes in one
+// launch depends on timing.
+template <typename T, bool PAIR>
+__device__ void advance_budget(const Walker& w0, const Params& P, long long sweep0, double sigma, uint64_t seed,
+                               Shared& sh) {
+  Ctl* c = w0.ctl;
+  const int n = w0.n, lim = P.step_limit > 0 ? min(n, P.step_limit) : n;
+  long long sw = c->pos_valid ? c->pos_sweep : sweep0;
+  int k = c->pos_valid ? c->pos_k : 0;
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0)
+      sh.iflag[9] = atomicAdd(P.budget_ctr, 1ull) < (unsigned long long)P.budget_total ? 1 : 0;
+    __syncthreads();
+    const int go = sh.iflag[9];
+    __syncthreads();
+    if (!go) break;
+    if (PAIR) af_step_begin<T>(w0, P, sh);
+    mc_step<T>(active_of(w0), P, k, seed, (uint32_t)sw, sigma, nullptr, nullptr, sh);
+    if (++k == lim) { k = 0; ++sw; }
+  }
+  if (threadIdx.x == 0) { c->pos_sweep = sw; c->pos_k = k; c->pos_valid = 1; }
+}
+
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
@@ -428,12 +458,17 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_sweep(const Walker* __restri
   const Walker& w = active_of(W[wi]);
   const uint64_t seed = seeds[wi];
   const int n = w.n;
+  if (P.budget_ctr) {
+    advance_budget<T, false>(W[wi], P, sweep0, sigma, seed, sh);
+    return;
+  }
   for (int s = 0; s < n_sweeps; ++s)
     for (int k = 0; k < (P.step_limit > 0 ? min(n, P.step_limit) : n); ++k) {
       const long long idx = (long long)n_sweeps * w.log_base + (long long)s * n + k;
       mc_step<T>(w, P, k, seed, (uint32_t)(sweep0 + s), sigma, acc_log ? acc_log + idx : nullptr,
                  ratio_log ? ratio_log + idx : nullptr, sh);
     }
+  if (threadIdx.x == 0) w.ctl->pos_valid = 0;  // every walker is at particle 0 of the next sweep
 }
 
 // Persistent sweeps with background refactorisation: a cluster of two CTAs per walker,
@@ -454,14 +489,19 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_sweep_pair(const Walker* __r
   }
   const uint64_t seed = seeds[wi];
   const int n = w0.n;
-  for (int s = 0; s < n_sweeps; ++s)
-    for (int k = 0; k < (P.step_limit > 0 ? min(n, P.step_limit) : n); ++k) {
-      af_step_begin<T>(w0, P, sh);
-      const Walker& w = active_of(w0);
-      const long long idx = (long long)n_sweeps * w.log_base + (long long)s * n + k;
-      mc_step<T>(w, P, k, seed, (uint32_t)(sweep0 + s), sigma, acc_log ? acc_log + idx : nullptr,
-                 ratio_log ? ratio_log + idx : nullptr, sh);
-    }
+  if (P.budget_ctr) {
+    advance_budget<T, true>(w0, P, sweep0, sigma, seed, sh);
+  } else {
+    for (int s = 0; s < n_sweeps; ++s)
+      for (int k = 0; k < (P.step_limit > 0 ? min(n, P.step_limit) : n); ++k) {
+        af_step_begin<T>(w0, P, sh);
+        const Walker& w = active_of(w0);
+        const long long idx = (long long)n_sweeps * w.log_base + (long long)s * n + k;
+        mc_step<T>(w, P, k, seed, (uint32_t)(sweep0 + s), sigma, acc_log ? acc_log + idx : nullptr,
+                   ratio_log ? ratio_log + idx : nullptr, sh);
+      }
+    if (threadIdx.x == 0) w0.ctl->pos_valid = 0;
+  }
   if (threadIdx.x == 0) af_finish(w0, launch_id);
 }
 

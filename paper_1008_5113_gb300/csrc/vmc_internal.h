@@ -86,6 +86,8 @@ cudaError_t launch_bench_T(const LaunchCfg& L, const Walker* W, int nwalk, const
 // least four fit, else 8 KB.  Fills tri_sf, y_half, y_smem, y_bytes, ring_slots,
 // slot_bytes, dsm_bytes.
 void plan_smem(int ybytes, int budget, Params& P, bool allow_sf);
+// Entries of an expanded row of the grouped triangular solves (a multiple of 4).
+int expanded_row_cap(int capLU);
 
 // host-side geometry and layout
 struct Layout {

@@ -180,6 +180,41 @@ __device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, boo
       const int* cl = st + pad4(nr + 1);
       const T* vl = (const T*)(cl + pad4(ne));
       const T* dv = (const T*)((const unsigned char*)vl + pad16((int)sizeof(T) * ne));
+      if (hd.w) {
+        // grouped form: the rows of a segment (group) are independent; each is a dot
+        // product with z = [solution | input] (y points at the solution part)
+        for (int sgi = 0; sgi < nseg; ++sgi) {
+          const int4 sm = seg[sgi];
+          const int r0 = sm.x, sr = sm.y, gs = sm.z;
+          const int G = 1 << gs;
+          const int gl = tid & (G - 1);
+          const int ng = nct >> gs;
+          for (int base = 0; base < sr; base += ng) {  // same trip count in every lane
+            const int i = r0 + base + (tid >> gs);
+            const bool on = base + (tid >> gs) < sr;
+            T part = 0, part2 = 0;
+            int r = 0;
+            if (on) {
+              r = rws[i];
+              const int e = st[i + 1];
+              int t = st[i] + gl;
+              for (; t + G < e; t += 2 * G) {
+                part += vl[t] * y[cl[t]];
+                part2 += vl[t + G] * y[cl[t + G]];
+              }
+              if (t < e) part += vl[t] * y[cl[t]];
+              part += part2;
+            }
+            for (int o = G >> 1; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o, G);
+            if (on && gl == 0) y[r] = part;
+          }
+          asm volatile("bar.sync 1, %0;" ::"r"(nct) : "memory");  // group barrier (consumers)
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.ebar[slot]);
+        if (++slot == S) { slot = 0; parity ^= 1u; }
+        continue;
+      }
       for (int sgi = 0; sgi < nseg; ++sgi) {
         const int4 sm = seg[sgi];
         const int r0 = sm.x, sr = sm.y;
@@ -380,6 +415,17 @@ template <typename T>
 __device__ __forceinline__ const T* tri_both(const Walker& w, const Params& P, const T* v, Shared& sh) {
   const int n = w.n, tid = threadIdx.x, nt = blockDim.x;
   T* y = P.y_smem ? (T*)dyn_smem() : (T*)w.tv;
+  if (grouped_solves(w, P)) {
+    // z layouts: L reads [y_L | v] and writes y_L; U reads [x | y_L] and writes x
+    T* x = y;
+    T* yl = y + n;
+    T* vin = y + 2 * n;
+    for (int i = tid; i < n; i += nt) vin[i] = v[i];
+    __syncthreads();
+    tri_staged<T>(w, P, false, yl, sh);
+    tri_staged<T>(w, P, true, x, sh);
+    return x;
+  }
   if (P.tri_sf) {
     T* x2 = (T*)(dyn_smem() + P.y_half);
     for (int i = tid; i < n; i += nt) { y[i] = Pending<T>::value(); x2[i] = Pending<T>::value(); }
@@ -490,12 +536,12 @@ __device__ __noinline__ void precond_apply(const Walker& w, const Params& P, con
 }
 
 // Dot products <V_k, wv> for k = 0..nk-1 into out[k]; if mon, also ||V_{nk-1} - wv||^2
-// into out[nk].  One warp per dot.  Ends synchronised.
+// into out[nk] and ||wv||^2 into out[nk + 1].  One warp per dot.  Ends synchronised.
 template <typename T>
 __device__ __forceinline__ void multi_dot(const T* __restrict__ V, int n, int nk, const T* __restrict__ wv,
                                           double* out, bool mon) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int total = nk + (mon ? 1 : 0);
+  const int total = nk + (mon ? 2 : 0);
   for (int k = wid; k < total; k += nw) {
     T a0 = 0, a1 = 0;
     if (k < nk) {
@@ -503,9 +549,11 @@ __device__ __forceinline__ void multi_dot(const T* __restrict__ V, int n, int nk
       int i = lane;
       for (; i + 32 < n; i += 64) { a0 += vk[i] * wv[i]; a1 += vk[i + 32] * wv[i + 32]; }
       if (i < n) a0 += vk[i] * wv[i];
-    } else {
+    } else if (k == nk) {
       const T* vk = V + (size_t)(nk - 1) * n;
       for (int i = lane; i < n; i += 32) { const T d = vk[i] - wv[i]; a0 += d * d; }
+    } else {
+      for (int i = lane; i < n; i += 32) a0 += wv[i] * wv[i];
     }
     const double s = warp_sum((double)a0 + (double)a1);
     if (lane == 0) out[k] = s;
@@ -541,28 +589,40 @@ __device__ __noinline__ int gmres_inner(const Walker& w, const Params& P, double
     if (tid == 0) {
       Ctl* c = w.ctl;
       c->cyc[PH_SPMV] += to - ts;
-      // SpMV: values + indices, x read, y write; CGS2: two projection passes over
-      // V_0..V_j and w, two update passes, the normalisation
+      // SpMV: values + indices, x read, y write; the first Gram-Schmidt pass: projections
+      // (V_0..V_j and w read) and update (V_0..V_j and w read, w written), normalisation
       c->alg_bytes += c->nnz_A * (sizeof(T) + 4) + (double)n * (2 * sizeof(T) + 4) +
-                      (double)n * sizeof(T) * (4.0 * (j + 1) + 8.0);
+                      (double)n * sizeof(T) * (2.0 * (j + 1) + 6.0);
     }
-    multi_dot<T>(V, n, j + 1, wv, sh.h1, true);          // projections + monitor
+    multi_dot<T>(V, n, j + 1, wv, sh.h1, true);          // projections, monitor, ||w||^2
     mon2 = fmax(mon2, sh.h1[j + 1]);
+    const double w2 = sh.h1[j + 2];
+    T nrm_t = 0;
     for (int i = tid; i < n; i += nt) {
       T acc = wv[i];
       for (int k = 0; k <= j; ++k) acc -= (T)sh.h1[k] * V[(size_t)k * n + i];
       wv[i] = acc;
-    }
-    __syncthreads();
-    multi_dot<T>(V, n, j + 1, wv, sh.h2, false);         // second Gram-Schmidt pass
-    T nrm_t = 0;
-    for (int i = tid; i < n; i += nt) {
-      T acc = wv[i];
-      for (int k = 0; k <= j; ++k) acc -= (T)sh.h2[k] * V[(size_t)k * n + i];
-      wv[i] = acc;
       nrm_t += acc * acc;
     }
-    const double nrm = sqrt(block_sum((double)nrm_t, sh));
+    double nrm2 = block_sum((double)nrm_t, sh);
+    // second Gram-Schmidt pass only when the first cancelled much of w: ||w'|| < ||w|| / sqrt(2)
+    // (Daniel, Gragg, Kaufman, Stewart 1976); else its coefficients are taken as zero
+    if (2.0 * nrm2 < w2) {
+      if (tid == 0) w.ctl->alg_bytes += (double)n * sizeof(T) * (2.0 * (j + 1) + 3.0);  // the second pass
+      multi_dot<T>(V, n, j + 1, wv, sh.h2, false);
+      nrm_t = 0;
+      for (int i = tid; i < n; i += nt) {
+        T acc = wv[i];
+        for (int k = 0; k <= j; ++k) acc -= (T)sh.h2[k] * V[(size_t)k * n + i];
+        wv[i] = acc;
+        nrm_t += acc * acc;
+      }
+      nrm2 = block_sum((double)nrm_t, sh);
+    } else {
+      if (tid <= j) sh.h2[tid] = 0.0;
+      __syncthreads();
+    }
+    const double nrm = sqrt(nrm2);
     const T sc = nrm > 0.0 ? (T)(1.0 / nrm) : (T)0;
     for (int i = tid; i < n; i += nt) wv[i] *= sc;
     if (tid == 0) {

@@ -132,7 +132,8 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   const int m = p.gmres_m, mu = std::max(1, p.max_updates);
   const int pmax = p.lfil_extra >= 0 ? p.lfil_extra : (cap + 1) / 2;
   const int capLU = (cap + pmax + 2 + 3) / 4 * 4;
-  const size_t sbytes = (size_t)n * (256 + 12 * (size_t)capLU);
+  const int exmax = expanded_row_cap(capLU);
+  const size_t sbytes = (size_t)n * (256 + 12 * (size_t)std::max(capLU, exmax));
 
   // carve the walker workspace out of the scratch array
   Off o;
@@ -153,11 +154,13 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   const size_t oUuv = o.take<char>((size_t)mu * kMaxU * Tsz), oUul = o.take<int>(mu);
   const size_t oG = o.take<double>((size_t)kMaxUpd * kMaxUpd);
   const size_t oV = o.take<char>((size_t)(m + 1) * n * Tsz), oZk = o.take<char>((size_t)m * n * Tsz);
-  const size_t oTv = o.take<char>((size_t)n * Tsz), oX = o.take<double>(n), oRr = o.take<double>(n);
+  const size_t oTv = o.take<char>((size_t)3 * n * Tsz), oX = o.take<double>(n), oRr = o.take<double>(n);
   const size_t oPac = o.take<int>(cap), oPav = o.take<double>(cap), oPuc = o.take<int>(kMaxU);
   const size_t oPuv = o.take<double>(kMaxU), oMeta = o.take<int4>(n + 1), oLnc = o.take<int>(n + 1);
   const size_t oSeg = o.take<int4>(2 * (size_t)n + 2);
   const size_t oUh = o.take<double2>(n);
+  const size_t oExl = o.take<int>(n), oExc = o.take<int>((size_t)n * exmax), oExv = o.take<double>((size_t)n * exmax);
+  const size_t oGp = o.take<int>(n + 1);
   const size_t oCtl = o.take<Ctl>(1), oW = o.take<Walker>(1);
   const size_t used = o.off;
   if (used > kNoAllocBytes)
@@ -181,6 +184,9 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   W.u_col = (int*)(base + oUc); W.u_val64 = (double*)(base + oUv); W.ustream = base + oUs; W.u_len = (int*)(base + oUl);
   W.u_dinv64 = (double*)(base + oUd);
   W.u_head = (double2*)(base + oUh);
+  W.exmax = exmax;
+  W.ex_len = (int*)(base + oExl); W.ex_col = (int*)(base + oExc); W.ex_val = (double*)(base + oExv);
+  W.gptr = (int*)(base + oGp);
   W.lchunk = (int2*)(base + oCh); W.uchunk = W.lchunk + (n + 1);
   W.perm = (int*)(base + oPm); W.iperm = (int*)(base + oIp); W.lev_l = (int*)(base + oLvl); W.lev_u = (int*)(base + oUvl);
   W.l_lvl_ptr = (int*)(base + oLlp); W.l_lvl_rows = (int*)(base + oLlr);
@@ -208,6 +214,7 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   P.trig_its = p.trigger_its > 0 ? p.trigger_its : 40;
   P.ilu_variant = (p.ilutp_variant >= 0 && p.ilutp_variant <= 2) ? p.ilutp_variant : 0;
   P.warp_rows = std::min(std::max(p.trisolve_warp_rows, 0), 32);
+  P.tri_group = p.trisolve == 1 ? 1 : std::min(std::max(p.trisolve_group, 1), 64);
   P.step_limit = 0;
   // shared-memory plan for a single walker CTA
   int dev = 0, optin = 0;
@@ -215,7 +222,7 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int stat = kernel_static_smem(fp64);
   if (optin <= 0 || stat <= 0) return fail(VMC_ERR_CUDA, "no usable CUDA device");
-  const int ybytes = (int)(((size_t)n * Tsz + 127) / 128 * 128);
+  const int ybytes = (int)(((size_t)(P.tri_group > 1 ? 3 : 1) * n * Tsz + 127) / 128 * 128);
   const int budget = optin - stat;
   plan_smem(ybytes, budget, P, p.trisolve == 1);
   const LaunchCfg L{s, p.block_threads ? p.block_threads : 256, fp64, (size_t)P.dsm_bytes};

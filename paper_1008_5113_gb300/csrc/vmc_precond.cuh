@@ -911,17 +911,21 @@ __device__ __noinline__ int ilutp_warp_hash(const Walker& w, const Params& P, Sh
 // chunks.  Block-wide (packing by thread 0: sequential over levels, and over rows
 // only inside levels that must be split).
 // ---------------------------------------------------------------------------
+// Grouped form (expanded = true): the segments are groups of consecutive levels and the
+// rows are the expanded rows of expand_groups (no diagonal array; chunk header .w = 1).
 template <typename T>
-__device__ int build_stream(const Walker& w, const Params& P, bool upper, int nlev, Shared& sh) {
+__device__ int build_stream(const Walker& w, const Params& P, bool upper, int nlev, Shared& sh,
+                            bool expanded = false) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  const int* lptr = upper ? w.u_lvl_ptr : w.l_lvl_ptr;
+  const int* lptr = expanded ? w.gptr : (upper ? w.u_lvl_ptr : w.l_lvl_ptr);
   const int* rows = upper ? w.u_lvl_rows : w.l_lvl_rows;
-  const int* len = upper ? w.u_len : w.l_len;
-  const int* colv = upper ? w.u_col : w.l_col;
-  const double* valv = upper ? w.u_val64 : w.l_val64;
+  const int* len = expanded ? w.ex_len : (upper ? w.u_len : w.l_len);
+  const int* colv = expanded ? w.ex_col : (upper ? w.u_col : w.l_col);
+  const double* valv = expanded ? w.ex_val : (upper ? w.u_val64 : w.l_val64);
   int2* tab = upper ? w.uchunk : w.lchunk;
   unsigned char* stream = upper ? w.ustream : w.lstream;
-  const int tsz = (int)sizeof(T), capLU = w.capLU;
+  const int tsz = (int)sizeof(T), capLU = expanded ? w.exmax : w.capLU;
+  const bool with_dv = upper && !expanded;
   const int SB = P.slot_bytes;
   const int nct = nt - 32;  // consumer threads of the solve
   // entries per level and the level's lane-group size (warp per level).  The group size
@@ -959,38 +963,38 @@ __device__ int build_stream(const Walker& w, const Params& P, bool upper, int nl
       const int gsl = w.lvl_nchunk[lev] >> 28;
       int gw = gsl;
       while (gw > 0 && (lr << gw) > 32) --gw;
-      const int wmode = (lr <= P.warp_rows && (lr << gw) <= 32) ? gw + 1 : 0;
+      const int wmode = (!expanded && lr <= P.warp_rows && (lr << gw) <= 32) ? gw + 1 : 0;
       const int lgs = gsl | (wmode << 8);
-      if (cs < kMaxSeg && chunk_bytes(cs + 1, cr + lr, ce + le, tsz, upper) <= SB) {
+      if (cs < kMaxSeg && chunk_bytes(cs + 1, cr + lr, ce + le, tsz, with_dv) <= SB) {
         w.seg_meta[nseg++] = make_int4(q, lr, le, lgs);  // the whole level joins the open chunk
         ++cs; cr += lr; ce += le;
         continue;
       }
       while (q < qe) {  // close the open chunk if any, then pieces of this level
-        if (cs > 0 && (cs == kMaxSeg || chunk_bytes(cs + 1, cr + 1, ce + len[rows[q]], tsz, upper) > SB)) {
+        if (cs > 0 && (cs == kMaxSeg || chunk_bytes(cs + 1, cr + 1, ce + len[rows[q]], tsz, with_dv) > SB)) {
           w.chunk_meta[nch] = make_int4(c_seg0, cs, cr, ce);
-          w.lvl_cur[nch] = chunk_bytes(cs, cr, ce, tsz, upper);
+          w.lvl_cur[nch] = chunk_bytes(cs, cr, ce, tsz, with_dv);
           ++nch; c_seg0 = nseg; cs = 0; cr = 0; ce = 0;
         }
         const int q0 = q;
         int pr = 0, pe = 0;
         while (q < qe) {
           const int L = len[rows[q]];
-          if ((cr + pr) > 0 && chunk_bytes(cs + 1, cr + pr + 1, ce + pe + L, tsz, upper) > SB) break;
+          if ((cr + pr) > 0 && chunk_bytes(cs + 1, cr + pr + 1, ce + pe + L, tsz, with_dv) > SB) break;
           ++pr; pe += L; ++q;
         }
         w.seg_meta[nseg++] = make_int4(q0, pr, pe, lgs);
         ++cs; cr += pr; ce += pe;
         if (q < qe) {  // the slot is full: close it
           w.chunk_meta[nch] = make_int4(c_seg0, cs, cr, ce);
-          w.lvl_cur[nch] = chunk_bytes(cs, cr, ce, tsz, upper);
+          w.lvl_cur[nch] = chunk_bytes(cs, cr, ce, tsz, with_dv);
           ++nch; c_seg0 = nseg; cs = 0; cr = 0; ce = 0;
         }
       }
     }
     if (cs > 0) {
       w.chunk_meta[nch] = make_int4(c_seg0, cs, cr, ce);
-      w.lvl_cur[nch] = chunk_bytes(cs, cr, ce, tsz, upper);
+      w.lvl_cur[nch] = chunk_bytes(cs, cr, ce, tsz, with_dv);
       ++nch;
     }
     sh.iflag[2] = nch;
@@ -1013,7 +1017,7 @@ __device__ int build_stream(const Walker& w, const Params& P, bool upper, int nl
     int* cl = st + pad4(nr + 1);
     T* vl = (T*)(cl + pad4(ne));
     T* dv = (T*)((unsigned char*)vl + pad16(tsz * ne));
-    if (lane == 0) *(int4*)base = make_int4(nseg, nr, ne, 0);
+    if (lane == 0) *(int4*)base = make_int4(nseg, nr, ne, expanded ? 1 : 0);
     if (lane < kMaxSlots) ((int2*)(base + 16))[lane] = c + 1 + lane < nch_total ? tab[c + 1 + lane] : make_int2(0, 0);
     int rbase = 0, carry = 0;
     for (int sgi = 0; sgi < nseg; ++sgi) {
@@ -1033,7 +1037,7 @@ __device__ int build_stream(const Walker& w, const Params& P, bool upper, int nl
         if (i < sr) {
           rws[rbase + i] = r;
           st[rbase + i] = carry + inc - L;
-          if (upper) dv[rbase + i] = (T)w.u_dinv64[r];
+          if (with_dv) dv[rbase + i] = (T)w.u_dinv64[r];
         }
         carry += __shfl_sync(0xffffffffu, inc, 31);
       }
@@ -1052,6 +1056,132 @@ __device__ int build_stream(const Walker& w, const Params& P, bool upper, int nl
   }
   __syncthreads();
   return nch_total;
+}
+
+// ---------------------------------------------------------------------------
+// Grouped triangular solves (a partitioned inverse of the factor).  Consecutive levels
+// of L (of U) are merged into groups of at most P.tri_group levels; every row of a group
+// is expanded by substituting the rows of the same group it depends on, so that it
+// reads only the input vector v and solution entries of earlier groups:
+//   L:  y_r = v_r - sum_c L_rc y_c          ->  y_r = sum_q a_rq v_q + sum_{c earlier} b_rc y_c
+//   U:  x_r = (y_r - sum_c U_rc x_c) / U_rr  ->  x_r = sum_q a_rq y_q + sum_{c earlier} b_rc x_c
+// (q over the row and its ancestors inside the group).  The rows of a group are then
+// independent, and the solve needs one barrier per group instead of one per level.  The
+// operator is the same as the level-by-level substitution in exact arithmetic (the
+// coefficients are formed in FP64 and rounded once to the working precision).  Indices
+// of the expanded rows address z = [solution | input]: c < n the solution entry c, n + q
+// the input entry q.  A level joins the open group only while every expanded row of it
+// stays within w.exmax entries; otherwise it starts a new group.
+// Block-wide; one warp per row with a hash accumulator of 2 exmax slots in the dynamic
+// shared memory (idle after the factorisation).  Writes w.gptr (row pointer of each
+// group into the level-ordered rows), w.ex_len/ex_col/ex_val; returns the group count.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __noinline__ int expand_groups(const Walker& w, const Params& P, bool upper, int nlev, Shared& sh) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int n = w.n, capLU = w.capLU, EX = w.exmax;
+  const int* lptr = upper ? w.u_lvl_ptr : w.l_lvl_ptr;
+  const int* rows = upper ? w.u_lvl_rows : w.l_lvl_rows;
+  const int* flen = upper ? w.u_len : w.l_len;
+  const int* fcol = upper ? w.u_col : w.l_col;
+  const double* fval = upper ? w.u_val64 : w.l_val64;
+  const int* lev = upper ? w.lev_u : w.lev_l;
+  const int hs = group_hash_slots(EX);  // per-warp table: at most half full
+  const int hmask = hs - 1;
+  int* hkey = reinterpret_cast<int*>(dyn_smem()) + (size_t)wid * hs * 3;  // keys, then values (8-byte aligned)
+  double* hval = reinterpret_cast<double*>(hkey + hs + (hs & 1));
+  auto add = [&](int key, double v, int& cnt, bool& over, bool active) {
+    // lanes with active = true add distinct keys; returns the updated count (uniform)
+    bool ins = false;
+    int h = 0;
+    if (active) {
+      h = (int)(((unsigned)key * 0x9E3779B1u) >> 7) & hmask;
+      for (int probe = 0; probe < hs; ++probe) {
+        const int k = hkey[h];
+        if (k == key) { hval[h] += v; break; }
+        if (k == -1) {
+          const int old = atomicCAS(&hkey[h], -1, key);
+          if (old == -1) { hval[h] = v; ins = true; break; }
+          if (old == key) { hval[h] += v; break; }
+        }
+        h = (h + 1) & hmask;
+      }
+    }
+    cnt += __popc(__ballot_sync(0xffffffffu, ins));
+    if (cnt > EX) over = true;
+    __syncwarp();
+  };
+  // expand the rows of level lv with the open group starting at level g; returns true
+  // (block-uniform) when a row exceeded exmax entries
+  auto expand_level = [&](int lv, int g) -> bool {
+    bool any_over = false;
+    for (int q = lptr[lv] + wid; q < lptr[lv + 1]; q += nw) {
+      const int r = rows[q];
+      for (int i = lane; i < hs; i += 32) hkey[i] = -1;
+      __syncwarp();
+      const double d = upper ? w.u_dinv64[r] : 1.0;
+      int cnt = 0;
+      bool over = false;
+      add(n + r, d, cnt, over, lane == 0);
+      const int L = flen[r];
+      const int* rc = fcol + (size_t)r * capLU;
+      const double* rv = fval + (size_t)r * capLU;
+      for (int t0 = 0; t0 < L; t0 += 32) {  // dependencies on earlier groups
+        const int t = t0 + lane;
+        const bool act = t < L && lev[rc[t]] < g;
+        add(act ? rc[t] : 0, act ? -d * rv[t] : 0.0, cnt, over, act);
+      }
+      for (int t = 0; t < L && !over; ++t) {  // dependencies inside the group: substitute
+        const int c = rc[t];
+        if (lev[c] < g) continue;
+        const double coef = -d * rv[t];
+        const int el = w.ex_len[c];
+        const int* ec = w.ex_col + (size_t)c * EX;
+        const double* ev = w.ex_val + (size_t)c * EX;
+        for (int e0 = 0; e0 < el; e0 += 32) {
+          const int e = e0 + lane;
+          add(e < el ? ec[e] : 0, e < el ? coef * ev[e] : 0.0, cnt, over, e < el);
+        }
+      }
+      // write the expanded row (slot order)
+      int outc = 0;
+      for (int i0 = 0; i0 < hs; i0 += 32) {
+        const int i = i0 + lane;
+        const bool k = !over && hkey[i] != -1;
+        const unsigned m = __ballot_sync(0xffffffffu, k);
+        const int slot = outc + __popc(m & lanemask_lt());
+        if (k && slot < EX) {
+          w.ex_col[(size_t)r * EX + slot] = hkey[i];
+          w.ex_val[(size_t)r * EX + slot] = hval[i];
+        }
+        outc += __popc(m);
+      }
+      if (lane == 0) w.ex_len[r] = over ? 0 : min(outc, EX);
+      any_over |= over;
+      __syncwarp();
+    }
+    const int o = block_max_int(any_over ? 1 : 0, sh);  // ends synchronised
+    return o != 0;
+  };
+  int g0 = 0, ngrp = 0;
+  if (tid == 0) w.gptr[0] = 0;
+  for (int lv = 0; lv < nlev; ++lv) {
+    const bool join = lv > 0 && lv - g0 < P.tri_group;
+    bool newg = !join;
+    if (join && expand_level(lv, g0)) newg = true;
+    if (newg) {
+      if (lv > 0) {
+        ++ngrp;
+        if (tid == 0) w.gptr[ngrp] = lptr[lv];
+      }
+      g0 = lv;
+      expand_level(lv, lv);
+    }
+  }
+  ++ngrp;
+  if (tid == 0) w.gptr[ngrp] = lptr[nlev];
+  __syncthreads();
+  return ngrp;
 }
 
 // Block-wide: relabel U columns to factor labels, compute U levels (warp 0,
@@ -1103,8 +1233,18 @@ __device__ __noinline__ void relabel_and_levels(const Walker& w, const Params& P
   for (int r = tid; r < n; r += nt) w.u_lvl_rows[atomicAdd(&w.lvl_cur[w.lev_u[r]], 1)] = r;
   if (tid == 0) { w.ctl->nlev_l = nll; w.ctl->nlev_u = nlu; }
   __syncthreads();
-  const int ncl = build_stream<T>(w, P, false, nll, sh);
-  const int ncu = build_stream<T>(w, P, true, nlu, sh);
+  int ncl, ncu;
+  if (grouped_solves(w, P)) {
+    const int gl = expand_groups<T>(w, P, false, nll, sh);
+    ncl = build_stream<T>(w, P, false, gl, sh, true);
+    const int gu = expand_groups<T>(w, P, true, nlu, sh);
+    ncu = build_stream<T>(w, P, true, gu, sh, true);
+    if (tid == 0) { w.ctl->ngrp_l = gl; w.ctl->ngrp_u = gu; }
+  } else {
+    ncl = build_stream<T>(w, P, false, nll, sh);
+    ncu = build_stream<T>(w, P, true, nlu, sh);
+    if (tid == 0) { w.ctl->ngrp_l = nll; w.ctl->ngrp_u = nlu; }
+  }
   if (tid == 0) { w.ctl->nchunk_l = ncl; w.ctl->nchunk_u = ncu; }
   fence_proxy_async_global();  // the streams are read next by bulk (async-proxy) copies
   __syncthreads();

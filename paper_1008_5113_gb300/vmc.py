@@ -46,7 +46,8 @@ class vmc_solver_params(C.Structure):
                 ("block_threads", C.c_int), ("sm_refresh", C.c_int), ("refactor_lag", C.c_int),
                 ("refactor_reorder", C.c_int), ("trisolve", C.c_int),
                 ("graphs", C.c_int), ("trigger_rtol", C.c_double), ("trigger_its", C.c_int), ("sweep_moves", C.c_int),
-                ("ilutp_variant", C.c_int), ("trisolve_warp_rows", C.c_int)]
+                ("ilutp_variant", C.c_int), ("trisolve_warp_rows", C.c_int),
+                ("trisolve_group", C.c_int)]
 
 
 class vmc_stats(C.Structure):
@@ -61,13 +62,15 @@ class vmc_stats(C.Structure):
                 ("ilu_rows", C.c_int64), ("ilu_elims", C.c_int64), ("ilu_cand", C.c_int64),
                 ("chunks_L", C.c_int), ("chunks_U", C.c_int), ("refactors_async", C.c_int64),
                 ("async_wait_cycles", C.c_int64), ("async_factor_cycles", C.c_int64), ("factor_set", C.c_int),
-                ("async_lag", C.c_int), ("max_updates", C.c_int), ("trigger_iterations", C.c_int64),
+                ("async_lag", C.c_int), ("max_updates", C.c_int), ("groups_L", C.c_int), ("groups_U", C.c_int),
+                ("trigger_iterations", C.c_int64),
                 ("reorders_skipped", C.c_int64)]
 
 
 class vmc_tune_trial(C.Structure):
     _fields_ = [("engine", C.c_int), ("block_threads", C.c_int), ("max_updates", C.c_int),
-                ("refactor_lag", C.c_int), ("ratios_per_s", C.c_double), ("status", C.c_int)]
+                ("refactor_lag", C.c_int), ("ratios_per_s", C.c_double), ("status", C.c_int),
+                ("lfil_extra", C.c_int)]
 
 
 # name -> (restype, argtypes); every symbol the header declares
@@ -86,6 +89,9 @@ _SIG = {
     "vmc_sweep": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vmc_sweep_async": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vmc_synchronize": (C.c_int, [C.c_void_p]),
+    "vmc_advance_async": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p]),
+    "vmc_advance": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p]),
+    "vmc_get_progress": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "vmc_kinetic_energy": (C.c_int, [C.c_void_p, C.c_void_p]),
     "vmc_get_stats": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "vmc_reset_stats": (C.c_int, [C.c_void_p]),
@@ -105,6 +111,8 @@ _SIG = {
     "vmc_noalloc_last_error": (C.c_char_p, []),
     "vmc_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int,
                                C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "vmc_autotune_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_int64,
+                                     C.c_double, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -236,6 +244,26 @@ def vmc_sweep_async(ctx, n_sweeps: int, sigma: float, seeds_dev, accept_log_dev=
                                  _p(ratio_log_dev)), ctx)
 
 
+def vmc_advance_async(ctx, total_moves: int, sigma: float, seeds_dev) -> None:
+    _check(lib().vmc_advance_async(ctx, int(total_moves), float(sigma), _p(seeds_dev)), ctx)
+
+
+def vmc_advance(ctx, total_moves: int, sigma: float, seeds) -> np.ndarray:
+    """Budgeted advance with host seeds; returns every walker's accepted-move count."""
+    s = np.ascontiguousarray(seeds, dtype=np.uint64)
+    acc = np.zeros(len(s), dtype=np.int64)
+    _check(lib().vmc_advance(ctx, int(total_moves), float(sigma), _p(s), _p(acc)), ctx)
+    return acc
+
+
+def vmc_get_progress(ctx, walker: int):
+    """(sweep, particle) of walker's next move."""
+    sw = C.c_int64(0)
+    k = C.c_int(0)
+    _check(lib().vmc_get_progress(ctx, walker, C.byref(sw), C.byref(k)), ctx)
+    return sw.value, k.value
+
+
 def vmc_synchronize(ctx) -> None:
     _check(lib().vmc_synchronize(ctx), ctx)
 
@@ -362,14 +390,21 @@ def params(**kw) -> vmc_solver_params:
     return p
 
 
-def vmc_autotune(systems, params: vmc_solver_params, seeds, jitter: float, sigma: float, steps: int, stream=None):
-    """Returns (the tuned parameters, the list of trials as dicts)."""
+def vmc_autotune(systems, params: vmc_solver_params, seeds, jitter: float, sigma: float, steps: int, stream=None,
+                 xyz=None, sweep0: int = 0):
+    """Returns (the tuned parameters, the list of trials as dicts).  xyz: optional start state
+    (every walker's positions, walker-major) with its sweep index sweep0."""
     arr = (vmc_system * len(systems))(*[vmc_system(int(K), int(lat), float(a), float(k), float(rc))
                                         for (K, lat, a, k, rc) in systems])
     p = vmc_solver_params.from_buffer_copy(params)
     s = np.ascontiguousarray(seeds, dtype=np.uint64)
+    x = None
+    if xyz is not None:
+        if isinstance(xyz, (list, tuple)):
+            xyz = np.concatenate([np.asarray(v, dtype=np.float64).reshape(-1) for v in xyz])
+        x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
     trials = (vmc_tune_trial * 16)()
     nt = C.c_int(0)
-    _check(lib().vmc_autotune(arr, len(systems), C.byref(p), _p(s), float(jitter), float(sigma), int(steps), trials, 16,
-                              C.byref(nt), _stream_handle(stream)))
+    _check(lib().vmc_autotune_state(arr, len(systems), C.byref(p), _p(s), float(jitter), _p(x), int(sweep0),
+                                    float(sigma), int(steps), trials, 16, C.byref(nt), _stream_handle(stream)))
     return p, [{name: getattr(trials[i], name) for name, _ in vmc_tune_trial._fields_} for i in range(nt.value)]

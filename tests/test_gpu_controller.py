@@ -66,9 +66,12 @@ def test_monitor_trigger_reorders(vmc, reference, prec):
 
 
 def test_nonconvergence_trigger_and_restarts(vmc, reference):
-    acc, rat, st = _run(vmc, precision=0, gmres_m=3, max_restarts=40)
+    """GMRES(3) needs many restarts; a tolerance of 1e-12 to be reached within 3 iterations
+    makes every solve count as not converged (reorder + refactor for the next moves)."""
+    acc, rat, st = _run(vmc, precision=0, gmres_m=3, max_restarts=40, trigger_rtol=1e-12, trigger_its=3)
     _check(rat, acc, reference)
     assert st["reorder_noconv"] > 10 and st["outer_passes"] > 2 * st["proposals"]
+    assert st["trigger_iterations"] > 3 * st["proposals"]
 
 
 def test_slow_convergence_trigger(vmc, reference):

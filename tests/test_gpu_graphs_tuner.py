@@ -74,7 +74,9 @@ def test_autotune_picks_a_valid_mapping(vmc):
     p, trials = vmc.vmc_autotune(systems, vmc.params(precision=1), [1, 2, 3, 4], wl.jitter, wl.sigma, 96)
     assert len(trials) >= 7 and all(t["status"] == 0 and t["ratios_per_s"] > 0 for t in trials)
     best = max(trials, key=lambda t: t["ratios_per_s"])
-    assert (p.engine, p.block_threads, p.max_updates) == (best["engine"], best["block_threads"], best["max_updates"])
+    assert (p.engine, p.block_threads, p.max_updates, p.lfil_extra) == (best["engine"], best["block_threads"],
+                                                                         best["max_updates"], best["lfil_extra"])
+    assert {t["lfil_extra"] for t in trials} >= {-1, 16, 32, 48}   # the fill limits were tried
     assert any(t["refactor_lag"] > 0 for t in trials)       # the walker-pair mapping was tried
     assert {t["engine"] for t in trials} >= {vmc.ENGINE_PERSISTENT, vmc.ENGINE_STEP}
     # the tuned parameters reproduce the oracle's chain
@@ -93,3 +95,14 @@ def test_autotune_picks_a_valid_mapping(vmc):
         assert abs(r_ref[upto] ** 2 - u_ref[upto]) < TIE
     lim = np.where(np.abs(r_ref[:upto]) >= 1e-3, RTOL * np.abs(r_ref[:upto]), ATOL)
     assert np.all(np.abs(rat[:upto] - r_ref[:upto]) <= lim) and upto > 100
+
+
+def test_autotune_from_a_given_state(vmc):
+    """Trials can start from a supplied state (e.g. an equilibrated one) and sweep index."""
+    wl = WL.PLAIN_216
+    s = O.system(6, 0, wl.a, wl.kappa, wl.r_c)
+    R0 = np.stack([O.initial_positions(s, w, wl.jitter) for w in (1, 2)])
+    R, _, _ = O.chains(s, [1, 2], wl.sigma, R0, 5, solver=O.SOLVER_SHERMAN_MORRISON)
+    p, trials = vmc.vmc_autotune(wl.systems() * 2, vmc.params(precision=1), [1, 2], wl.jitter, wl.sigma, 64,
+                                 xyz=[R[0], R[1]], sweep0=5)
+    assert trials and all(t["status"] == 0 and t["ratios_per_s"] > 0 for t in trials)

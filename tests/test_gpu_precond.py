@@ -160,3 +160,29 @@ def test_shared_memory_ilutp_gives_the_dense_row_factors(vmc, hard_positions, pr
     assert np.array_equal(L0.view(np.uint64), L1.view(np.uint64))
     assert np.array_equal(U0.view(np.uint64), U1.view(np.uint64))
     assert np.array_equal(a0, a1) and np.array_equal(r0.view(np.uint64), r1.view(np.uint64))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_grouped_triangular_solves_apply_the_same_preconditioner(vmc, hard_positions, prec):
+    """The grouped (partitioned-inverse) triangular solves apply the operator of the
+    level-by-level substitution: same factors, results equal to rounding, far fewer
+    synchronisation steps."""
+    R = hard_positions
+    rng = np.random.default_rng(5)
+    v = rng.standard_normal(1000)
+    out = {}
+    for group in (1, 8):
+        ctx = vmc.vmc_create([(10, 0, 1.0, 2.0, 1.5)], vmc.params(precision=prec, trisolve_group=group))
+        try:
+            vmc.vmc_set_positions(ctx, 0, R)
+            L, U, perm = vmc.vmc_get_factors(ctx, 0)
+            out[group] = (vmc.vmc_apply_preconditioner(ctx, 0, v), L, U, vmc.vmc_get_stats(ctx, 0))
+        finally:
+            vmc.vmc_destroy(ctx)
+    z1, L1, U1, s1 = out[1]
+    z8, L8, U8, s8 = out[8]
+    assert np.array_equal(L1, L8) and np.array_equal(U1, U8)
+    tol = 1e-12 if prec == 0 else 1e-5
+    assert np.abs(z8 - z1).max() <= tol * np.abs(z1).max()
+    assert s1["groups_L"] == s1["levels_L"] and s1["groups_U"] == s1["levels_U"]
+    assert s8["groups_L"] < s8["levels_L"] and s8["groups_U"] < s8["levels_U"]
