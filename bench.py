@@ -254,6 +254,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-kernels", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the larger configurations' legs")
     ap.add_argument("--headline-only", action="store_true", help="skip every leg after the headline")
     ap.add_argument("--no-autotune", action="store_true", help="fixed solver layout instead of the autotuner's")
     args = ap.parse_args()
@@ -311,8 +312,10 @@ def main():
     # ---- solver layout: the autotuner's pick, from the saved state ---------------------
     def tuned(prec):
         base = vmc.params(precision=prec)
-        if args.no_autotune:
-            base.lfil_extra = 32 if prec == vmc.PREC_FP64 else 64
+        if args.no_autotune:  # the layout the autotuner picks for this workload (persistent, 256 threads)
+            base.lfil_extra = 32
+            base.max_updates = 32
+            base.refactor_lag = 0 if prec == vmc.PREC_FP64 else 16
             return base, []
         t1 = time.perf_counter()
         p, trials = vmc.vmc_autotune(systems, base, seeds, JITTER, SIGMA, 64, stream=stream, xyz=state,
@@ -457,6 +460,76 @@ def main():
             log(f"plain: {time.perf_counter() - t0:.1f} s; {plain:.0f} ratios/s")
         elif not args.no_plain:
             skipped.append("plain")
+    if rank == 0 and not args.no_configs and not args.headline_only:
+        # ---- the larger configurations, mixed precision, budgeted advance: each warmed up
+        #      from its start state by a budgeted advance (a few sweeps' worth of moves: 20
+        #      sweeps of these batches do not fit a benchmark run), then one timed step,
+        #      against the one-walker-per-launch FP64 path at the same size from the same
+        #      state (walker 0) -------------------------------------------------------------
+        from paper_1008_5113_gb300 import workloads as WLS
+
+        cfg_out = {}
+        # fill limit 32 (the autotuner's pick at n = 1000) except for the large matrices of
+        # kappa 1, r_c 2, whose rows then outgrow the factorisation's working row: the default
+        for wl, warm_moves, step_moves, plain_moves, lfil in ((WLS.MIXED_4096, 2 * 4096, 64, 32, 32),
+                                                              (WLS.UNEVEN_320, 1000, 64, 32, 32),
+                                                              (WLS.LARGE_32768, 0, 16, 8, -1)):
+            if over_budget():
+                skipped.append(wl.name)
+                continue
+            t0 = time.perf_counter()
+            csys = wl.systems()
+            cnw = len(csys)
+            cseeds = wl.seeds()
+            csd = torch.tensor(cseeds, dtype=torch.int64, device="cuda")
+            pm = vmc.params(precision=vmc.PREC_MIXED, lfil_extra=lfil, trisolve_group=1)
+            c = vmc.vmc_create(csys, pm, stream=stream)
+            vmc.vmc_init_positions(c, cseeds, wl.jitter)
+            if warm_moves:
+                vmc.vmc_advance_async(c, cnw * warm_moves, wl.sigma, csd)
+                vmc.vmc_synchronize(c)
+            prog = [vmc.vmc_get_progress(c, w) for w in range(cnw)]
+            xyz = np.concatenate([vmc.vmc_get_positions(c, w).reshape(-1) for w in range(cnw)])
+            vmc.vmc_reset_stats(c)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            vmc.vmc_advance_async(c, cnw * step_moves, wl.sigma, csd)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            vmc.vmc_synchronize(c)
+            ms = e0.elapsed_time(e1)
+            cst = [vmc.vmc_get_stats(c, w) for w in range(cnw)]
+            vmc.vmc_destroy(c)
+            P_ = sum(x["proposals"] for x in cst)
+            rec = {"walkers": cnw, "n": sorted({K ** 3 for K in wl.Ks}), "rate": P_ / (ms / 1000.0), "lfil": lfil,
+                   "moves_timed": P_, "its_per_ratio": sum(x["inner_iterations"] for x in cst) / P_,
+                   "accept_rate": sum(x["accepts"] for x in cst) / P_,
+                   "start": f"sweep 0 + a budgeted advance of {warm_moves} moves a walker (walker 0 at sweep "
+                            f"{prog[0][0]}, particle {prog[0][1]}); not equilibrated",
+                   "its_hist": [sum(x["its_hist"][b] for x in cst) for b in range(40)]}
+            # plain FP64 one-walker-per-launch path: walker 0 from the same state
+            n0 = wl.Ks[0] ** 3
+            pp = vmc.params(precision=vmc.PREC_FP64, engine=vmc.ENGINE_PLAIN, lfil_extra=lfil, sweep_moves=plain_moves)
+            cp = vmc.vmc_create(csys[:1], pp, stream=stream)
+            vmc.vmc_set_positions_all(cp, xyz[:3 * n0])
+            vmc.vmc_set_sweep_count(cp, prog[0][0])
+            torch.cuda.synchronize()
+            e0.record(stream)
+            vmc.vmc_sweep_async(cp, 1, wl.sigma, csd[:1])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            vmc.vmc_synchronize(cp)
+            pms = e0.elapsed_time(e1)
+            psts = vmc.vmc_get_stats(cp, 0)
+            vmc.vmc_destroy(cp)
+            rec["plain_fp64_rate"] = psts["proposals"] / (pms / 1000.0)
+            rec["plain_fp64_sample"] = f"walker 0 (n = {n0}), {psts['proposals']} moves from particle 0 of its sweep"
+            rec["speedup_vs_plain"] = rec["rate"] / rec["plain_fp64_rate"]
+            cfg_out[wl.name] = rec
+            log(f"config {wl.name}: {time.perf_counter() - t0:.1f} s; {rec['rate']:.0f} ratios/s, plain "
+                f"{rec['plain_fp64_rate']:.0f}")
+        extra["configs"] = cfg_out
     if rank == 0 and not args.no_kernels and not args.headline_only:
         # ---- per-kernel rooflines at the HBM-sized configurations (CTA per walker; n = 4096
         #      with 256 walkers, n = 32768 with 152 = one per SM): triangular solves and SpMV,
@@ -468,7 +541,10 @@ def main():
                 skipped.append(f"kernels_sc{K}_k{kap:g}")
                 continue
             t0 = time.perf_counter()
-            ctxk = vmc.vmc_create([(K, 0, A, kap, rc)] * nwk, vmc.params(precision=vmc.PREC_MIXED), stream=stream)
+            # level-by-level solves: with two walker CTAs an SM (n = 4096) the solves are bound by
+            # work, where grouping loses; at n = 32768 two solve vectors do not fit shared memory
+            ctxk = vmc.vmc_create([(K, 0, A, kap, rc)] * nwk, vmc.params(precision=vmc.PREC_MIXED, trisolve_group=1),
+                                  stream=stream)
             vmc.vmc_init_positions(ctxk, list(range(1, nwk + 1)), JITTER)
             reps = 40 if K == 16 else (10 if kap == KAPPA else 4)
             for which, name in ((0, "trisolve"), (1, "spmv")):

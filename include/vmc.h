@@ -215,20 +215,25 @@ typedef struct {
   double ratios_per_s; /* measured determinant ratios per second (0 when the trial failed) */
   int status;          /* vmc_status of the trial                                        */
   int lfil_extra;      /* ILUTP fill limit of the trial (-1: half the average row count)   */
+  int trisolve_group;  /* triangular-solve grouping of the trial (1: level by level)       */
 } vmc_tune_trial;
 
 /* Autotuner: picks the launch mapping and solver layout for these walkers by timing
- * short trials on the device.  Candidates: a CTA pair per walker with background
- * refactorisation (when the pairs fit), a CTA per walker (persistent), one launch per
- * step (STEP engine); 128 or 256 threads per CTA; then max_updates of 32, 64 or 128 for
- * the best of those; then the ILUTP fill limit lfil_extra of -1 (half the average row
- * count, the paper's), 16, 32 or 48 for the best of those.  Each trial creates a context
+ * short trials on the device.  First the ILUTP fill limit lfil_extra: -1 (half the
+ * average row count, the paper's), 16, 32 or 48, with the default mapping; then, at the
+ * best of those, the mapping: a CTA pair per walker with background refactorisation
+ * (when the pairs fit), a CTA per walker (persistent), one launch per step (STEP engine),
+ * with 128 or 256 threads per CTA; then max_updates of 32, 64 or 128 for the best of
+ * those; then grouped (8 levels) against level-by-level triangular solves (trisolve_group).
+ * Each trial creates a context
  * from `params` with the candidate's fields, starts the walkers from `seeds` and
- * `jitter`, runs one untimed and one timed partial sweep of `steps` moves per walker
- * (proposal width sigma) and destroys the context.  The mapping and the fill limit do
+ * `jitter`, makes n_walkers x `steps` moves twice, untimed then timed (proposal width
+ * sigma) -- as a budgeted advance with the persistent engine (the batch's throughput),
+ * as a partial sweep of `steps` moves per walker with the STEP engine -- and destroys the
+ * context.  The mapping and the fill limit do
  * not change the method's results -- only its cost, and the rounding.
  * params (in/out): the base parameters; on return engine, block_threads, max_updates,
- * refactor_lag and lfil_extra hold the fastest trial's.  trials (nullable): receives up to
+ * refactor_lag, lfil_extra and trisolve_group hold the fastest trial's.  trials (nullable): receives up to
  * max_trials trial records, *n_trials (nullable) their number.  stream as in vmc_create.
  * Returns VMC_ERR_INVALID on bad arguments or a DENSE_SM engine, the first failure if
  * every trial fails, else VMC_OK. */

@@ -535,13 +535,16 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
       *out = ctx;
       return fail(ctx, VMC_ERR_CUDA, "no usable CUDA device (shared-memory attributes unavailable)");
     }
-    const int nvec = ctx->P.tri_group > 1 ? 3 : 1;  // grouped solves keep three vectors
-    const int ybytes = (int)(((size_t)nvec * ctx->max_n * Tsz + 127) / 128 * 128);
+    // grouped solves keep two vectors in shared memory; when two do not fit, one (the
+    // level-by-level solve in place) -- walkers whose two vectors fit it still group
+    const int ybytes1 = (int)(((size_t)ctx->max_n * Tsz + 127) / 128 * 128);
+    const int ybytes = ctx->P.tri_group > 1 ? (int)(((size_t)2 * ctx->max_n * Tsz + 127) / 128 * 128) : ybytes1;
     const int budget1 = optin - stat;
     const int budget2 = per_sm / 2 - 1024 - stat;
     int budget = budget1;
     if (n_walkers > nsm && budget2 >= ybytes + 2 * kSlotBytes) budget = budget2;
     plan_smem(ybytes, budget, ctx->P, p.trisolve == 1);
+    if (!ctx->P.y_smem && ybytes != ybytes1) plan_smem(ybytes1, budget, ctx->P, p.trisolve == 1);
     ctx->smem = (size_t)ctx->P.dsm_bytes;
   }
   const size_t ctl_off = cv.take<Ctl>(n_walkers);
@@ -1293,11 +1296,21 @@ static vmc_status tune_trial(const vmc_system* systems, int nw, const vmc_solver
     c->P.step_limit = steps;
     long long moves = 0;
     for (int w = 0; w < nw; ++w) moves += std::min(c->hw[w].n, steps);
+    // the persistent engine makes the trial's moves as a budgeted advance (the batch's
+    // throughput); the others a partial sweep of `steps` moves per walker
+    const bool budget = p.engine == VMC_ENGINE_PERSISTENT;
+    auto trial = [&]() -> vmc_status {
+      if (budget) {
+        c->P.step_limit = 0;
+        return vmc_advance_async(c, moves, sigma, c->d_seeds);
+      }
+      return enqueue_sweeps(c, 1, sigma, c->d_seeds, nullptr, nullptr);
+    };
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = VMC_ERR_CUDA;
-    if (st == VMC_OK) st = enqueue_sweeps(c, 1, sigma, c->d_seeds, nullptr, nullptr);  // untimed
-    if (st == VMC_OK && xyz) st = start();  // the timed sweep from the same state
+    if (st == VMC_OK) st = trial();  // untimed
+    if (st == VMC_OK && xyz) st = start();  // the timed trial from the same state
     if (st == VMC_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = VMC_ERR_CUDA;
-    if (st == VMC_OK) st = enqueue_sweeps(c, 1, sigma, c->d_seeds, nullptr, nullptr);  // timed
+    if (st == VMC_OK) st = trial();  // timed
     if (st == VMC_OK && cudaEventRecord(e1, c->stream) != cudaSuccess) st = VMC_ERR_CUDA;
     if (st == VMC_OK) st = check_walker_status(c);
     float ms = 0.0f;
@@ -1317,7 +1330,7 @@ extern "C" vmc_status vmc_autotune_state(const vmc_system* systems, int n_walker
   if (!systems || !params || !seeds || n_walkers <= 0 || steps <= 0 || !(sigma >= 0.0) || !(jitter >= 0.0) ||
       sweep0 < 0 || (trials && max_trials < 0) || params->engine == VMC_ENGINE_DENSE_SM)
     return VMC_ERR_INVALID;
-  struct Cand { int engine, threads, mu, lag, lfil; };
+  struct Cand { int engine, threads, mu, lag, lfil, group; };
   std::vector<vmc_tune_trial> done;
   vmc_status first_err = VMC_OK;
   auto run = [&](const Cand& cd) -> double {
@@ -1327,34 +1340,50 @@ extern "C" vmc_status vmc_autotune_state(const vmc_system* systems, int n_walker
     p.max_updates = cd.mu;
     p.refactor_lag = cd.lag;
     p.lfil_extra = cd.lfil;
+    p.trisolve_group = cd.group;
     double rate = 0.0;
     int lag = 0, mu = cd.mu;
     const vmc_status st = tune_trial(systems, n_walkers, p, seeds, jitter, xyz, sweep0, sigma, steps, stream, &rate,
                                      &lag, &mu);
     if (st != VMC_OK && first_err == VMC_OK) first_err = st;
-    vmc_tune_trial t{cd.engine, cd.threads, mu, lag, st == VMC_OK ? rate : 0.0, (int)st, cd.lfil};
+    vmc_tune_trial t{cd.engine, cd.threads, mu, lag, st == VMC_OK ? rate : 0.0, (int)st, cd.lfil, cd.group};
     done.push_back(t);
     return st == VMC_OK ? rate : 0.0;
   };
-  // phase 1: mapping x CTA size at the given chain length and fill limit
-  const int mu0 = params->max_updates, lf0 = params->lfil_extra;
+  // phase 1: the ILUTP fill limit (it decides how often the controller must reorder, which
+  // dominates the cost of every other choice) with the default mapping
+  const int mu0 = params->max_updates;
   double best = -1.0;
-  Cand bc{VMC_ENGINE_PERSISTENT, 256, mu0, 0, lf0};
+  Cand bc{VMC_ENGINE_PERSISTENT, 256, mu0, -1, params->lfil_extra, params->trisolve_group};
+  for (int lf : {-1, 16, 32, 48}) {
+    Cand cd = bc;
+    cd.lfil = lf;
+    const double r = run(cd);
+    if (r > best) { best = r; bc = cd; }
+  }
+  // phase 2: mapping x CTA size at that fill limit
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const bool pairs_fit = auto_pairs_fit(systems, n_walkers, nsm) && (mu0 < 0 || mu0 >= 2);  // refactor_lag = -1's rule
+  const Cand b1 = bc;
   for (int threads : {128, 256}) {
-    const Cand cands[3] = {{VMC_ENGINE_PERSISTENT, threads, mu0, -1, lf0},
-                           {VMC_ENGINE_PERSISTENT, threads, mu0, 0, lf0},
-                           {VMC_ENGINE_STEP, threads, mu0, 0, lf0}};
+    const Cand cands[3] = {{VMC_ENGINE_PERSISTENT, threads, mu0, -1, b1.lfil, b1.group},
+                           {VMC_ENGINE_PERSISTENT, threads, mu0, 0, b1.lfil, b1.group},
+                           {VMC_ENGINE_STEP, threads, mu0, 0, b1.lfil, b1.group}};
     for (const Cand& cd : cands) {
-      if (cd.lag == -1 && !pairs_fit) continue;  // would be the same as the next candidate
+      if (cd.lag == -1 && (!pairs_fit || threads == 256)) continue;  // (256, -1) was phase 1's trial
+      if (cd.lag == 0 && cd.engine == VMC_ENGINE_PERSISTENT && threads == 256 && !pairs_fit) continue;
       const double r = run(cd);
-      if (r > best) { best = r; bc = cd; bc.lag = done.back().refactor_lag; bc.mu = done.back().max_updates; }
+      if (r > best) { best = r; bc = cd; }
     }
   }
-  // phase 2: chain length for the best mapping
+  {
+    // the record of the best trial holds the lag and chain length it ran with
+    for (const vmc_tune_trial& t : done)
+      if (t.status == VMC_OK && t.ratios_per_s == best) { bc.lag = t.refactor_lag; bc.mu = t.max_updates; }
+  }
+  // phase 3: chain length for the best mapping
   const int mu_best = bc.mu;
   for (int mu : {32, 64, 128}) {
     if (mu == mu_best || mu > kMaxUpd) continue;
@@ -1364,11 +1393,12 @@ extern "C" vmc_status vmc_autotune_state(const vmc_system* systems, int n_walker
     const double r = run(cd);
     if (r > best) { best = r; bc = cd; bc.lag = done.back().refactor_lag; }
   }
-  // phase 3: ILUTP fill limit for the best mapping and chain length
-  for (int lf : {-1, 16, 32, 48}) {
-    if (lf == bc.lfil) continue;
+  // phase 4: grouped or level-by-level triangular solves (grouping trades synchronisation
+  // for work: it wins where a walker's solve is latency-bound, loses where two walker CTAs
+  // share an SM and the work counts)
+  {
     Cand cd = bc;
-    cd.lfil = lf;
+    cd.group = bc.group > 1 ? 1 : 8;
     if (bc.lag > 0) cd.lag = -1;
     const double r = run(cd);
     if (r > best) { best = r; bc = cd; bc.lag = done.back().refactor_lag; }
@@ -1382,6 +1412,7 @@ extern "C" vmc_status vmc_autotune_state(const vmc_system* systems, int n_walker
   params->max_updates = bc.mu;
   params->refactor_lag = bc.lag;
   params->lfil_extra = bc.lfil;
+  params->trisolve_group = bc.group;
   return VMC_OK;
 }
 

@@ -210,15 +210,19 @@ struct __align__(16) Shared {
 };
 
 // Grouped triangular solves (expand_groups): on when asked for, the walker has the
-// scratch for the expanded rows, and one warp-sized hash accumulator per warp of the
-// CTA fits the dynamic shared memory.  Decided the same way at factorisation and solve.
+// scratch for the expanded rows, its two solve vectors fit the shared-memory solve area,
+// and one hash accumulator per warp of the CTA fits the dynamic shared memory (else the
+// level-by-level solve, in place on one vector).  Decided the same way at factorisation
+// and solve.
 __device__ __forceinline__ int group_hash_slots(int exmax) {
   int hs = 64;
   while (hs < 2 * exmax) hs <<= 1;
   return hs;
 }
+template <typename T>
 __device__ __forceinline__ bool grouped_solves(const Walker& w, const Params& P) {
-  return P.tri_group > 1 && w.ex_col != nullptr &&
+  return P.tri_group > 1 && w.ex_col != nullptr && P.y_smem &&
+         2 * (size_t)w.n * sizeof(T) <= (size_t)P.y_bytes &&  // both solve vectors in shared memory
          (size_t)(blockDim.x >> 5) * 12u * (size_t)group_hash_slots(w.exmax) <= (size_t)P.dsm_bytes;
 }
 

@@ -222,9 +222,11 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int stat = kernel_static_smem(fp64);
   if (optin <= 0 || stat <= 0) return fail(VMC_ERR_CUDA, "no usable CUDA device");
-  const int ybytes = (int)(((size_t)(P.tri_group > 1 ? 3 : 1) * n * Tsz + 127) / 128 * 128);
+  const int ybytes1 = (int)(((size_t)n * Tsz + 127) / 128 * 128);
+  const int ybytes = P.tri_group > 1 ? (int)(((size_t)2 * n * Tsz + 127) / 128 * 128) : ybytes1;
   const int budget = optin - stat;
   plan_smem(ybytes, budget, P, p.trisolve == 1);
+  if (!P.y_smem && ybytes != ybytes1) plan_smem(ybytes1, budget, P, p.trisolve == 1);
   const LaunchCfg L{s, p.block_threads ? p.block_threads : 256, fp64, (size_t)P.dsm_bytes};
 
   // clear the part of the scratch this call uses, then fill the inputs

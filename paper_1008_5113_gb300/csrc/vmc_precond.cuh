@@ -1069,9 +1069,11 @@ __device__ int build_stream(const Walker& w, const Params& P, bool upper, int nl
 // independent, and the solve needs one barrier per group instead of one per level.  The
 // operator is the same as the level-by-level substitution in exact arithmetic (the
 // coefficients are formed in FP64 and rounded once to the working precision).  Indices
-// of the expanded rows address z = [solution | input]: c < n the solution entry c, n + q
-// the input entry q.  A level joins the open group only while every expanded row of it
-// stays within w.exmax entries; otherwise it starts a new group.
+// of the expanded rows are offsets from the solution vector: c in [0, n) the solution
+// entry c; the input entry q at n + q for L (the input vector follows the solution) and
+// at q - n for U (it precedes it: the L solution is U's input).  A level joins the open
+// group only while every expanded row of it stays within w.exmax entries; otherwise it
+// starts a new group.
 // Block-wide; one warp per row with a hash accumulator of 2 exmax slots in the dynamic
 // shared memory (idle after the factorisation).  Writes w.gptr (row pointer of each
 // group into the level-ordered rows), w.ex_len/ex_col/ex_val; returns the group count.
@@ -1088,6 +1090,8 @@ __device__ __noinline__ int expand_groups(const Walker& w, const Params& P, bool
   const int* lev = upper ? w.lev_u : w.lev_l;
   const int hs = group_hash_slots(EX);  // per-warp table: at most half full
   const int hmask = hs - 1;
+  constexpr int kEmpty = (int)0x80000000;  // keys are offsets in [-n, 2n)
+  const int in_off = upper ? -n : n;
   int* hkey = reinterpret_cast<int*>(dyn_smem()) + (size_t)wid * hs * 3;  // keys, then values (8-byte aligned)
   double* hval = reinterpret_cast<double*>(hkey + hs + (hs & 1));
   auto add = [&](int key, double v, int& cnt, bool& over, bool active) {
@@ -1099,9 +1103,9 @@ __device__ __noinline__ int expand_groups(const Walker& w, const Params& P, bool
       for (int probe = 0; probe < hs; ++probe) {
         const int k = hkey[h];
         if (k == key) { hval[h] += v; break; }
-        if (k == -1) {
-          const int old = atomicCAS(&hkey[h], -1, key);
-          if (old == -1) { hval[h] = v; ins = true; break; }
+        if (k == kEmpty) {
+          const int old = atomicCAS(&hkey[h], kEmpty, key);
+          if (old == kEmpty) { hval[h] = v; ins = true; break; }
           if (old == key) { hval[h] += v; break; }
         }
         h = (h + 1) & hmask;
@@ -1117,12 +1121,12 @@ __device__ __noinline__ int expand_groups(const Walker& w, const Params& P, bool
     bool any_over = false;
     for (int q = lptr[lv] + wid; q < lptr[lv + 1]; q += nw) {
       const int r = rows[q];
-      for (int i = lane; i < hs; i += 32) hkey[i] = -1;
+      for (int i = lane; i < hs; i += 32) hkey[i] = kEmpty;
       __syncwarp();
       const double d = upper ? w.u_dinv64[r] : 1.0;
       int cnt = 0;
       bool over = false;
-      add(n + r, d, cnt, over, lane == 0);
+      add(in_off + r, d, cnt, over, lane == 0);
       const int L = flen[r];
       const int* rc = fcol + (size_t)r * capLU;
       const double* rv = fval + (size_t)r * capLU;
@@ -1147,7 +1151,7 @@ __device__ __noinline__ int expand_groups(const Walker& w, const Params& P, bool
       int outc = 0;
       for (int i0 = 0; i0 < hs; i0 += 32) {
         const int i = i0 + lane;
-        const bool k = !over && hkey[i] != -1;
+        const bool k = !over && hkey[i] != kEmpty;
         const unsigned m = __ballot_sync(0xffffffffu, k);
         const int slot = outc + __popc(m & lanemask_lt());
         if (k && slot < EX) {
@@ -1234,7 +1238,7 @@ __device__ __noinline__ void relabel_and_levels(const Walker& w, const Params& P
   if (tid == 0) { w.ctl->nlev_l = nll; w.ctl->nlev_u = nlu; }
   __syncthreads();
   int ncl, ncu;
-  if (grouped_solves(w, P)) {
+  if (grouped_solves<T>(w, P)) {
     const int gl = expand_groups<T>(w, P, false, nll, sh);
     ncl = build_stream<T>(w, P, false, gl, sh, true);
     const int gu = expand_groups<T>(w, P, true, nlu, sh);

@@ -70,7 +70,7 @@ class vmc_stats(C.Structure):
 class vmc_tune_trial(C.Structure):
     _fields_ = [("engine", C.c_int), ("block_threads", C.c_int), ("max_updates", C.c_int),
                 ("refactor_lag", C.c_int), ("ratios_per_s", C.c_double), ("status", C.c_int),
-                ("lfil_extra", C.c_int)]
+                ("lfil_extra", C.c_int), ("trisolve_group", C.c_int)]
 
 
 # name -> (restype, argtypes); every symbol the header declares
