@@ -257,6 +257,8 @@ def main():
     ap.add_argument("--no-configs", action="store_true", help="skip the larger configurations' legs")
     ap.add_argument("--headline-only", action="store_true", help="skip every leg after the headline")
     ap.add_argument("--no-autotune", action="store_true", help="fixed solver layout instead of the autotuner's")
+    ap.add_argument("--layout", default="pairs", choices=["pairs", "inline"],
+                    help="with --no-autotune: a factor CTA per walker (background refactorisation) or in-line")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -312,10 +314,12 @@ def main():
     # ---- solver layout: the autotuner's pick, from the saved state ---------------------
     def tuned(prec):
         base = vmc.params(precision=prec)
-        if args.no_autotune:  # the layout the autotuner picks for this workload (persistent, 256 threads)
+        if args.no_autotune:  # the layouts the autotuner picks for this workload (persistent, 256 threads)
             base.lfil_extra = 32
-            base.max_updates = 32
-            base.refactor_lag = 0 if prec == vmc.PREC_FP64 else 16
+            if args.layout == "pairs":
+                base.max_updates, base.refactor_lag = 128, 64
+            else:
+                base.max_updates, base.refactor_lag = 128, 0
             return base, []
         t1 = time.perf_counter()
         p, trials = vmc.vmc_autotune(systems, base, seeds, JITTER, SIGMA, 64, stream=stream, xyz=state,
