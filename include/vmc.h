@@ -150,9 +150,15 @@ typedef struct {
                           the input vector and the solution of earlier groups; the solve then
                           synchronises once per group instead of once per level.  The same
                           operator as level-by-level substitution in exact arithmetic.  A level
-                          whose expanded rows would exceed max(capacity + 4, min(2 capacity,
-                          160)) entries starts a new group.  0 or 1: level by level; ignored
-                          with trisolve = 1 (8) */
+                          whose expanded rows would exceed the expanded-row capacity
+                          (trisolve_row_cap) starts a new group.  0 or 1: level by level;
+                          ignored with trisolve = 1 (8) */
+  int trisolve_row_cap; /* expanded-row capacity of the grouped solves, in entries: 0 = max(c + 4,
+                          min(2 c, 160)) with c the factor-row capacity; otherwise max(c + 4,
+                          this), at most 480 (0) */
+  int trisolve_lane_entries; /* triangular solves: each row is summed by a group of lanes sized
+                          for at most this many entries a lane on the level's (group's)
+                          longest row, <= 64; 0 = 2 in FP32, 8 in FP64 (0) */
 } vmc_solver_params;
 
 /* Per-walker statistics (Sec. 4 Tables 2 and 3 analogues). */
@@ -201,6 +207,8 @@ typedef struct {
                                 factors were those of a reorder + refactorisation of the very
                                 same matrix (no move accepted since): refactoring it again
                                 would reproduce them, so the solve only restarts           */
+  int64_t stream_bytes;      /* bytes of the L and U chunk streams at the last factorisation:
+                                what one preconditioner apply reads (grouped rows expanded)  */
 } vmc_stats;
 
 /* Fill p (host) with the defaults above; VMC_ERR_INVALID for NULL. */

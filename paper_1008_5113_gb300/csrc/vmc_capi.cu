@@ -20,8 +20,17 @@ using namespace vmc;
 // ---------------------------------------------------------------------------
 namespace vmc {
 
-int expanded_row_cap(int capLU) {
-  return (std::max(capLU + 4, std::min(2 * capLU, 160)) + 3) / 4 * 4;
+int expanded_row_cap(int capLU, int row_cap) {
+  const int c = row_cap > 0 ? row_cap : std::min(2 * capLU, 160);
+  return (std::max(capLU + 4, c) + 3) / 4 * 4;
+}
+
+// One factor row of either stream form (FP64, with its diagonal) fits the smallest ring slot.
+bool rows_fit_slot(int cap, int lfil_extra, int row_cap) {
+  const int pmax = lfil_extra >= 0 ? lfil_extra : (cap + 1) / 2;
+  const int capLU = (cap + pmax + 2 + 3) / 4 * 4;
+  const int mx = std::max(capLU, expanded_row_cap(capLU, row_cap));
+  return chunk_bytes(1, 1, mx, 8, true) <= kSlotBytes && chunk_bytes_grouped(1, 1, mx, 8) <= kSlotBytes;
 }
 
 void plan_smem(int ybytes, int budget, Params& P, bool allow_sf) {
@@ -127,6 +136,7 @@ struct vmc_ctx {
   Params P{};
   cudaStream_t stream = nullptr;
   int threads = 256;
+  int row_cap = 0;  // trisolve_row_cap
   bool fp64 = false;
   std::vector<Walker> hw;
   Walker* dW = nullptr;
@@ -222,6 +232,8 @@ extern "C" vmc_status vmc_default_params(vmc_solver_params* p) {
   p->ilutp_variant = 0;
   p->trisolve_warp_rows = 0;
   p->trisolve_group = 8;
+  p->trisolve_row_cap = 0;
+  p->trisolve_lane_entries = 0;
   return VMC_OK;
 }
 
@@ -344,6 +356,8 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   else if (p.ilutp_variant < 0 || p.ilutp_variant > 2) st = bad("ilutp_variant must be 0, 1 or 2");
   else if (p.trisolve_warp_rows < 0 || p.trisolve_warp_rows > 32) st = bad("trisolve_warp_rows must be in [0, 32]");
   else if (p.trisolve_group < 0 || p.trisolve_group > 64) st = bad("trisolve_group must be in [0, 64]");
+  else if (p.trisolve_row_cap < 0 || p.trisolve_row_cap > 480) st = bad("trisolve_row_cap must be in [0, 480]");
+  else if (p.trisolve_lane_entries < 0 || p.trisolve_lane_entries > 64) st = bad("trisolve_lane_entries must be in [0, 64]");
   else if (!(p.trigger_rtol < 1.0)) st = bad("trigger_rtol must be below 1");
   if (st != VMC_OK) { *out = ctx; return st; }
   ctx->fp64 = p.precision == VMC_PREC_FP64;
@@ -363,6 +377,8 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
   ctx->P.step_limit = p.sweep_moves;
   ctx->P.ilu_variant = p.ilutp_variant;
   ctx->P.warp_rows = p.trisolve_warp_rows;
+  ctx->row_cap = p.trisolve_row_cap;
+  ctx->P.lane_entries = p.trisolve_lane_entries > 0 ? p.trisolve_lane_entries : (ctx->fp64 ? 8 : 2);
   ctx->P.tri_group = p.trisolve == 1 ? 1 : std::max(1, p.trisolve_group);  // the sync-free solves read levels
   {
     // background refactorisation (persistent engine) when asked for, or by default when
@@ -397,6 +413,11 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
       *out = ctx;
       return VMC_ERR_INVALID;
     }
+    if (p.engine != VMC_ENGINE_DENSE_SM && !rows_fit_slot(lay[w].cap, p.lfil_extra, p.trisolve_row_cap)) {
+      ctx->err = std::string("walker ") + std::to_string(w) + ": factor rows longer than a stream slot (r_c or lfil_extra too large)";
+      *out = ctx;
+      return VMC_ERR_INVALID;
+    }
   }
   if (p.engine == VMC_ENGINE_DENSE_SM) {
     vmc_status ds = create_dense(ctx, lay);
@@ -415,7 +436,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     const int n = L.n, cap = L.cap;
     const int pmax = p.lfil_extra >= 0 ? p.lfil_extra : (cap + 1) / 2;
     const int capLU = (cap + pmax + 2 + 3) / 4 * 4;  // rows of 16-byte multiples (bulk copies)
-    const int exmax = expanded_row_cap(capLU);
+    const int exmax = expanded_row_cap(capLU, p.trisolve_row_cap);
     auto& o = offs[w];
     o.push_back(cv.take<double>((size_t)n * 3));       // 0 Z
     o.push_back(cv.take<int>(n));                      // 1 col_of_orb
@@ -621,7 +642,7 @@ extern "C" vmc_status vmc_create(const vmc_system* systems, int n_walkers, const
     W.u_head = (double2*)(A + o[ctx->pair ? 82 : 50]);
     {
       const size_t e0 = ctx->pair ? 84 : 51;
-      W.exmax = expanded_row_cap(W.capLU);
+      W.exmax = expanded_row_cap(W.capLU, ctx->row_cap);
       W.ex_len = (int*)(A + o[e0]);
       W.ex_col = (int*)(A + o[e0 + 1]);
       W.ex_val = (double*)(A + o[e0 + 2]);
@@ -1107,6 +1128,7 @@ extern "C" vmc_status vmc_get_stats(vmc_ctx* ctx, int walker, vmc_stats* out) {
   out->trigger_iterations = h.trig_its;
   out->groups_L = h.ngrp_l;
   out->groups_U = h.ngrp_u;
+  out->stream_bytes = h.stream_bytes;
   return VMC_OK;
 }
 

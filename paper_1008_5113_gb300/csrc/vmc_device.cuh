@@ -57,6 +57,7 @@ struct Ctl {
   int last_breakdown;
   int nchunk_l, nchunk_u;
   int ngrp_l, ngrp_u;  // barriers of the triangular solves (groups; = levels when not grouped)
+  long long stream_bytes;  // bytes of the L and U chunk streams (read by every preconditioner apply)
   double pend_r[3];
   double pend_ratio;
   double pend_grad[3], pend_lap;  // gradient / Laplacian at the pending position (when asked)
@@ -169,6 +170,7 @@ struct Params {
   int ilu_variant;  // 0: auto (hash working row where the dense one misses shared memory); 1: dense; 2: hash
   int warp_rows;    // levels of at most this many rows: triangular-solve rows by one warp, no barrier
   int tri_group;    // > 1: grouped triangular solves, at most this many levels per group
+  int lane_entries; // entries per lane the triangular solves' lane groups are sized for
   // budgeted advance of the persistent engine: the walkers claim moves one at a time from
   // *budget_ctr until budget_total are claimed (nullptr: fixed sweeps)
   unsigned long long* budget_ctr;
@@ -226,6 +228,49 @@ __device__ __forceinline__ bool grouped_solves(const Walker& w, const Params& P)
          (size_t)(blockDim.x >> 5) * 12u * (size_t)group_hash_slots(w.exmax) <= (size_t)P.dsm_bytes;
 }
 
+// ---- block-wide copies with several loads in flight per thread ---------------
+// A plain loop `dst[i] = src[i]` between pointers that may alias issues each load only
+// after the previous iteration's store, i.e. one memory latency per iteration; these
+// issue kCopyBatch loads before their stores.
+constexpr int kCopyBatch = 8;
+template <typename T>
+__device__ __forceinline__ void block_copy(T* dst, const T* src, int n) {
+  const int nt = blockDim.x;
+  for (int i0 = threadIdx.x; i0 < n; i0 += kCopyBatch * nt) {
+    T v[kCopyBatch];
+#pragma unroll
+    for (int k = 0; k < kCopyBatch; ++k) {
+      const int i = i0 + k * nt;
+      v[k] = i < n ? src[i] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < kCopyBatch; ++k) {
+      const int i = i0 + k * nt;
+      if (i < n) dst[i] = v[k];
+    }
+  }
+}
+// dst[idx[i]] = src[i]
+template <typename T>
+__device__ __forceinline__ void block_scatter(T* dst, const int* idx, const T* src, int n) {
+  const int nt = blockDim.x;
+  for (int i0 = threadIdx.x; i0 < n; i0 += kCopyBatch * nt) {
+    T v[kCopyBatch];
+    int d[kCopyBatch];
+#pragma unroll
+    for (int k = 0; k < kCopyBatch; ++k) {
+      const int i = i0 + k * nt;
+      v[k] = i < n ? src[i] : T(0);
+      d[k] = i < n ? idx[i] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kCopyBatch; ++k) {
+      const int i = i0 + k * nt;
+      if (i < n) dst[d[k]] = v[k];
+    }
+  }
+}
+
 // ---- dynamic shared memory, mbarriers and bulk (TMA) copies ----------------
 __device__ __forceinline__ unsigned char* dyn_smem() {
   extern __shared__ __align__(128) unsigned char vmc_dsm[];
@@ -248,6 +293,22 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// The same with an L2 eviction-priority policy (createpolicy): the chunk streams are
+// re-read by every preconditioner apply and are asked to stay in L2 ahead of data read
+// once per apply.
+__device__ __forceinline__ unsigned long long l2_policy_evict_last() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, unsigned bytes, unsigned long long* bar,
+                                              unsigned long long pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
       : "memory");
 }
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -307,6 +368,13 @@ __host__ __device__ __forceinline__ int pad16(int x) { return (x + 15) & ~15; }
 __host__ __device__ __forceinline__ int chunk_bytes(int nseg, int r, int e, int tsz, bool upper) {
   return kChunkHdr + 16 * nseg + 4 * pad4(r) + 4 * pad4(r + 1) + 4 * pad4(e) + pad16(tsz * e) +
          (upper ? pad16(tsz * r) : 0);
+}
+// Grouped form (header .w = 1): int4 seg[segments]; int4 rowdesc[r] {output index, first
+// entry, end entry, 0}; the entries: FP32 as (column bits, value) pairs of 8 bytes, FP64 as
+// an int column array then a double value array (12 bytes an entry: the streams of many
+// walkers share the L2).
+__host__ __device__ __forceinline__ int chunk_bytes_grouped(int nseg, int r, int e, int tsz) {
+  return kChunkHdr + 16 * nseg + 16 * r + (tsz == 4 ? pad16(8 * e) : pad16(4 * e) + pad16(8 * e));
 }
 
 // ---- warp / block reductions (fixed butterfly order: deterministic) ----------

@@ -284,6 +284,7 @@ __device__ void af_swap(const Walker& w0, const Params& P, Shared& sh) {
     c->nlev_l = sc->nlev_l; c->nlev_u = sc->nlev_u;
     c->ngrp_l = sc->ngrp_l; c->ngrp_u = sc->ngrp_u;
     c->nchunk_l = sc->nchunk_l; c->nchunk_u = sc->nchunk_u;
+    c->stream_bytes = sc->stream_bytes;
     c->nnz_LU = sc->nnz_LU; c->nnz_A = sc->nnz_A;
     c->p_lfil = sc->p_lfil; c->last_pivots = sc->last_pivots; c->last_breakdown = 0;
     c->active = c->af_target;
@@ -706,11 +707,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_bench(const Walker* __restri
       const long long t0 = clock64();
       const T* y = tri_both<T>(w, P, V, sh);
       if (threadIdx.x == 0) w.ctl->cyc[PH_TRI] += clock64() - t0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) Zk[w.perm[i]] = y[i];
+      block_scatter(Zk, w.perm, y, n);
       if (threadIdx.x == 0)
         w.ctl->alg_bytes += w.ctl->nnz_LU * (sizeof(T) + 4) + (double)n * (3 * sizeof(T) + 8);
     } else if (which == 1) {
-      spmv<T>(w, V, Zk);
+      spmv<T>(w, P, stage_x<T>(w, P, V), Zk);
       if (threadIdx.x == 0) w.ctl->alg_bytes += w.ctl->nnz_A * (sizeof(T) + 4) + (double)n * (2 * sizeof(T) + 4);
     } else {
       precond_apply<T>(w, P, V, Zk, sh);

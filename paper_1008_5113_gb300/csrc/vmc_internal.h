@@ -87,7 +87,8 @@ cudaError_t launch_bench_T(const LaunchCfg& L, const Walker* W, int nwalk, const
 // slot_bytes, dsm_bytes.
 void plan_smem(int ybytes, int budget, Params& P, bool allow_sf);
 // Entries of an expanded row of the grouped triangular solves (a multiple of 4).
-int expanded_row_cap(int capLU);
+int expanded_row_cap(int capLU, int row_cap);
+bool rows_fit_slot(int cap, int lfil_extra, int row_cap);
 
 // host-side geometry and layout
 struct Layout {

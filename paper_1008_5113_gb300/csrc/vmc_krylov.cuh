@@ -30,12 +30,22 @@ template <> struct Vec4<float> {
     const float4 q = *reinterpret_cast<const float4*>(p);
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
   }
+  // streaming load (evict first): data read once per apply
+  __device__ __forceinline__ void load_cs(const float* p) {
+    const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
 };
 template <> struct Vec4<double> {
   double v[4];
   __device__ __forceinline__ void load(const double* p) {
     const double2 a = *reinterpret_cast<const double2*>(p);
     const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+  __device__ __forceinline__ void load_cs(const double* p) {
+    const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldcs(reinterpret_cast<const double2*>(p + 2));
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
   }
 };
@@ -82,17 +92,30 @@ __device__ __forceinline__ X slot_dot(const int* __restrict__ cols, const T* __r
 }
 
 // y = A_p x: one particle's slot per thread, taken in slot order (consecutive threads
-// read consecutive slots), the result scattered to the slot's row of A_p.  (Two slots in
-// flight per thread, their loads issued together, measured slower: 90 against 62 us at
-// n = 4096 x 256 walkers.)
+// read consecutive slots), the result scattered to the slot's row of A_p.  (Measured
+// slower at n = 4096 x 256 walkers: two slots in flight per thread, 90 against 62 us; a
+// warp staging 32 slots through shared memory with coalesced loads, 72 against 56 us.)
 template <typename T>
-__device__ __forceinline__ void spmv(const Walker& w, const T* __restrict__ x, T* __restrict__ y) {
+__device__ __forceinline__ void spmv(const Walker& w, const Params& P, const T* __restrict__ x, T* __restrict__ y) {
   const T* av = a_vals<T>(w);
   const int n = w.n, cap = w.cap, nt = blockDim.x;
   for (int p = threadIdx.x; p < n; p += nt) {
     const int len = w.a_len[p], r = w.row_of_part[p];
     y[r] = slot_dot<T, T>(w.a_col + (size_t)p * cap, av + (size_t)p * cap, len, cap, x);
   }
+}
+
+// The SpMV's input vector, copied into the shared-memory solve-vector area when that
+// holds one (idle between preconditioner applies): the SpMV's gathers then read shared
+// memory instead of scattered global lines.  Block-wide; returns the vector to read.
+template <typename T>
+__device__ __forceinline__ const T* stage_x(const Walker& w, const Params& P, const T* x) {
+  if (!P.y_smem) return x;
+  T* xs = (T*)dyn_smem();
+  __syncthreads();
+  block_copy(xs, x, w.n);
+  __syncthreads();
+  return xs;
 }
 
 // Shared-memory ring of the stream chunks: one mbarrier per slot, initialised once
@@ -112,6 +135,32 @@ __device__ __forceinline__ void ring_init(Shared& sh, const Params& P) {
   __syncthreads();
 }
 
+// Entries of a grouped chunk (the layout of chunk_bytes_grouped): entry t is (column
+// offset, value).
+template <typename T>
+struct GroupedEntries;
+template <>
+struct GroupedEntries<float> {
+  const float2* p;
+  __device__ __forceinline__ GroupedEntries(const unsigned char* ent, int) : p((const float2*)ent) {}
+  __device__ __forceinline__ void get(int t, int& c, float& v) const {
+    const float2 e = p[t];
+    c = __float_as_int(e.x);
+    v = e.y;
+  }
+};
+template <>
+struct GroupedEntries<double> {
+  const int* c;
+  const double* v;
+  __device__ __forceinline__ GroupedEntries(const unsigned char* ent, int ne)
+      : c((const int*)ent), v((const double*)(ent + pad16(4 * ne))) {}
+  __device__ __forceinline__ void get(int t, int& cc, double& vv) const {
+    cc = c[t];
+    vv = v[t];
+  }
+};
+
 // Producer of the chunk streams (lane 0 of the last warp): streams the factor's chunks
 // into the ring with bulk copies, refilling a slot once the consumers have released it
 // (the slot's "empty" barrier).  Returns the cycles spent waiting for free slots.
@@ -124,6 +173,7 @@ __device__ __forceinline__ long long stream_chunks(const unsigned char* stream, 
   for (int k = 0; k < S && k < nch; ++k) pre[k] = tab[k];
   int slot = seq0 % S;
   int g = seq0;
+  const unsigned long long pol = l2_policy_evict_last();
   for (int c = 0; c < nch; ++c, ++g) {
     unsigned char* dst = ring + (size_t)slot * SB;
     if (g >= S) {  // the consumers must have released the slot's previous use
@@ -135,7 +185,7 @@ __device__ __forceinline__ long long stream_chunks(const unsigned char* stream, 
     // header of chunk c - S, still in this slot
     const int2 tc = c < S ? pre[c] : ((const int2*)(dst + 16))[S - 1];
     mbar_expect_tx(&sh.bar[slot], (unsigned)tc.y);
-    bulk_g2s(dst, stream + tc.x, (unsigned)tc.y, &sh.bar[slot]);
+    bulk_g2s_hint(dst, stream + tc.x, (unsigned)tc.y, &sh.bar[slot], pol);
     if (++slot == S) slot = 0;
   }
   return twait;
@@ -184,7 +234,10 @@ __device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, boo
       const T* dv = (const T*)((const unsigned char*)vl + pad16((int)sizeof(T) * ne));
       if (hd.w) {
         // grouped form: the rows of a segment (group) are independent; each is a dot
-        // product with z = [solution | input] (y points at the solution part)
+        // product with the solution and input vectors at offsets from y (row descriptor
+        // {output, first, end}; entries as (column, value) pairs)
+        const int4* desc = (const int4*)(ch + kChunkHdr + 16 * nseg);
+        const GroupedEntries<T> ent(ch + kChunkHdr + 16 * nseg + 16 * nr, ne);
         for (int sgi = 0; sgi < nseg; ++sgi) {
           const int4 sm = seg[sgi];
           const int r0 = sm.x, sr = sm.y, gs = sm.z;
@@ -194,18 +247,54 @@ __device__ __forceinline__ void tri_staged(const Walker& w, const Params& P, boo
           for (int base = 0; base < sr; base += ng) {  // same trip count in every lane
             const int i = r0 + base + (tid >> gs);
             const bool on = base + (tid >> gs) < sr;
-            T part = 0, part2 = 0;
+            T part = 0;
             int r = 0;
             if (on) {
-              r = rws[i];
-              const int e = st[i + 1];
-              int t = st[i] + gl;
-              for (; t + G < e; t += 2 * G) {
-                part += vl[t] * y[cl[t]];
-                part2 += vl[t + G] * y[cl[t + G]];
+              // expanded rows are long (up to exmax entries): FP32 keeps four entries in
+              // flight per lane; FP64 two (every extra partial sum costs an FP64 add)
+              const int4 d = desc[i];
+              r = d.x;
+              const int e = d.z;
+              int t = d.y + gl;
+              if constexpr (sizeof(T) == 4) {
+                T p1 = 0, p2 = 0, p3 = 0;
+                for (; t + 3 * G < e; t += 4 * G) {
+                  int c0, c1, c2, c3;
+                  T v0, v1, v2, v3;
+                  ent.get(t, c0, v0);
+                  ent.get(t + G, c1, v1);
+                  ent.get(t + 2 * G, c2, v2);
+                  ent.get(t + 3 * G, c3, v3);
+                  part += v0 * y[c0];
+                  p1 += v1 * y[c1];
+                  p2 += v2 * y[c2];
+                  p3 += v3 * y[c3];
+                }
+                for (; t < e; t += G) {
+                  int c0;
+                  T v0;
+                  ent.get(t, c0, v0);
+                  part += v0 * y[c0];
+                }
+                part = (part + p1) + (p2 + p3);
+              } else {
+                T p1 = 0;
+                for (; t + G < e; t += 2 * G) {
+                  int c0, c1;
+                  T v0, v1;
+                  ent.get(t, c0, v0);
+                  ent.get(t + G, c1, v1);
+                  part += v0 * y[c0];
+                  p1 += v1 * y[c1];
+                }
+                if (t < e) {
+                  int c0;
+                  T v0;
+                  ent.get(t, c0, v0);
+                  part += v0 * y[c0];
+                }
+                part += p1;
               }
-              if (t < e) part += vl[t] * y[cl[t]];
-              part += part2;
             }
             for (int o = G >> 1; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o, G);
             if (on && gl == 0) y[r] = part;
@@ -422,7 +511,7 @@ __device__ __forceinline__ const T* tri_both(const Walker& w, const Params& P, c
     // writes x into b (v is no longer needed) reading y_L at offset -n
     T* a = y;
     T* b = y + n;
-    for (int i = tid; i < n; i += nt) b[i] = v[i];
+    block_copy(b, v, n);
     __syncthreads();
     tri_staged<T>(w, P, false, a, sh);
     tri_staged<T>(w, P, true, b, sh);
@@ -436,7 +525,7 @@ __device__ __forceinline__ const T* tri_both(const Walker& w, const Params& P, c
     tri_syncfree<T>(w, P, true, y, x2, sh);
     return x2;
   }
-  for (int i = tid; i < n; i += nt) y[i] = v[i];
+  block_copy(y, v, n);
   __syncthreads();
   tri_staged<T>(w, P, false, y, sh);
   tri_staged<T>(w, P, true, y, sh);
@@ -457,7 +546,7 @@ __device__ __noinline__ void precond_apply(const Walker& w, const Params& P, con
     // factor values + indices, diagonal, v read, z write, the level-row records
     c->alg_bytes += c->nnz_LU * (sizeof(T) + 4) + (double)n * (3 * sizeof(T) + 8);
   }
-  for (int t = tid; t < n; t += nt) z[w.perm[t]] = y[t];
+  block_scatter(z, w.perm, y, n);
   __syncthreads();
   const int mu = w.ctl->n_upd;
   if (mu > 0) {
@@ -513,14 +602,15 @@ __device__ __noinline__ void precond_apply(const Walker& w, const Params& P, con
     }
     if (Gs) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // before the ring's next bulk copies
     __syncthreads();
-    // w = w_0 - sum_s z_hat_s c_s: row i of Zt is contiguous over s
+    // w = w_0 - sum_s z_hat_s c_s: row i of Zt is contiguous over s (streaming loads: the
+    // chain is read once per apply and should not push the chunk streams out of L2)
     for (int i = tid; i < n; i += nt) {
       const T* zr = Zt + (size_t)i * mcap;
       T acc = z[i];
       int s_ = 0;
       for (; s_ + 4 <= mu; s_ += 4) {
         Vec4<T> v;
-        v.load(zr + s_);
+        v.load_cs(zr + s_);
         acc -= v.v[0] * (T)sh.cupd[s_] + v.v[1] * (T)sh.cupd[s_ + 1] + v.v[2] * (T)sh.cupd[s_ + 2] +
                v.v[3] * (T)sh.cupd[s_ + 3];
       }
@@ -585,7 +675,7 @@ __device__ __noinline__ int gmres_inner(const Walker& w, const Params& P, double
     T* wv = V + (size_t)(j + 1) * n;
     precond_apply<T>(w, P, vj, zj, sh);
     const long long ts = clock64();
-    spmv<T>(w, zj, wv);
+    spmv<T>(w, P, stage_x<T>(w, P, zj), wv);
     __syncthreads();
     const long long to = clock64();
     if (tid == 0) {

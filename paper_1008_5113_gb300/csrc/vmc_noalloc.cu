@@ -117,12 +117,15 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   if (p.gmres_m < 1 || p.gmres_m > kMaxM || p.max_updates > kMaxUpd ||
       (p.precision != VMC_PREC_FP64 && p.precision != VMC_PREC_MIXED && p.precision != VMC_PREC_MIXED_F32ILU) ||
       (p.block_threads != 0 && (p.block_threads < 64 || p.block_threads > kMaxThreads || p.block_threads % 32)) ||
-      !(p.drop_tol >= 0.0) || !(p.permtol >= 0.0) || p.max_restarts < 0)
+      !(p.drop_tol >= 0.0) || !(p.permtol >= 0.0) || p.max_restarts < 0 || p.trisolve_row_cap < 0 ||
+      p.trisolve_row_cap > 480 || p.trisolve_lane_entries < 0 || p.trisolve_lane_entries > 64)
     return fail(VMC_ERR_INVALID, "invalid solver parameters");
   Layout lay;
   const char* why = "";
   if (make_layout(sys->K, sys->lattice, sys->a, sys->r_c, lay, &why)) return fail(VMC_ERR_INVALID, why);
   if (!(sys->kappa > 0.0)) return fail(VMC_ERR_INVALID, "kappa must be positive");
+  if (!rows_fit_slot(lay.cap, p.lfil_extra, p.trisolve_row_cap))
+    return fail(VMC_ERR_INVALID, "factor rows longer than a stream slot (r_c or lfil_extra too large)");
   const int n = lay.n, cap = lay.cap;
   if (k < 0 || k >= n) return fail(VMC_ERR_INVALID, "particle index out of range");
   for (int d = 0; d < 3; ++d)
@@ -132,7 +135,7 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   const int m = p.gmres_m, mu = std::max(1, p.max_updates);
   const int pmax = p.lfil_extra >= 0 ? p.lfil_extra : (cap + 1) / 2;
   const int capLU = (cap + pmax + 2 + 3) / 4 * 4;
-  const int exmax = expanded_row_cap(capLU);
+  const int exmax = expanded_row_cap(capLU, p.trisolve_row_cap);
   const size_t sbytes = (size_t)n * (256 + 12 * (size_t)std::max(capLU, exmax));
 
   // carve the walker workspace out of the scratch array
@@ -215,6 +218,7 @@ extern "C" vmc_status vmc_ratio_noalloc(const vmc_system* sys, const vmc_solver_
   P.ilu_variant = (p.ilutp_variant >= 0 && p.ilutp_variant <= 2) ? p.ilutp_variant : 0;
   P.warp_rows = std::min(std::max(p.trisolve_warp_rows, 0), 32);
   P.tri_group = p.trisolve == 1 ? 1 : std::min(std::max(p.trisolve_group, 1), 64);
+  P.lane_entries = p.trisolve_lane_entries > 0 ? std::min(p.trisolve_lane_entries, 64) : (fp64 ? 8 : 2);
   P.step_limit = 0;
   // shared-memory plan for a single walker CTA
   int dev = 0, optin = 0;

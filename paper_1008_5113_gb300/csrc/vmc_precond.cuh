@@ -926,13 +926,19 @@ __device__ int build_stream(const Walker& w, const Params& P, bool upper, int nl
   unsigned char* stream = upper ? w.ustream : w.lstream;
   const int tsz = (int)sizeof(T), capLU = expanded ? w.exmax : w.capLU;
   const bool with_dv = upper && !expanded;
+  auto cbytes = [&](int ns, int r, int e) {
+    return expanded ? chunk_bytes_grouped(ns, r, e, tsz) : chunk_bytes(ns, r, e, tsz, with_dv);
+  };
   const int SB = P.slot_bytes;
   const int nct = nt - 32;  // consumer threads of the solve
   // entries per level and the level's lane-group size (warp per level).  The group size
   // is a property of the level, not of the chunk a piece of it lands in, so the rounding
-  // of every row is independent of the slot size.  Enough lanes for <= 2 entries per lane
-  // on the level's longest row (the level barrier waits for it), while the rows still fit
-  // the consumer threads once.  Packed as entries | gs << 28 (entries < 2^28 for K <= 64).
+  // of every row is independent of the slot size.  Enough lanes for <= P.lane_entries
+  // entries per lane on the level's longest row (the level barrier waits for it), while
+  // the rows still fit the consumer threads once.  Few entries a lane (FP32: 2) keep the
+  // dependent chain short; FP64 takes more (8), because every lane-group reduction step
+  // is an FP64 add and GB300's FP64 pipe issues few per clock.  Packed as
+  // entries | gs << 28 (entries < 2^28 for K <= 64).
   for (int lev = wid; lev < nlev; lev += nw) {
     int e = 0, ml = 0;
     for (int q = lptr[lev] + lane; q < lptr[lev + 1]; q += 32) {
@@ -944,7 +950,7 @@ __device__ int build_stream(const Walker& w, const Params& P, bool upper, int nl
     ml = warp_max_int(ml);
     const int lr = lptr[lev + 1] - lptr[lev];
     int gs = 0;
-    while (gs < 5 && (2 << gs) < ml && (lr << (gs + 1)) <= nct) ++gs;
+    while (gs < 5 && (P.lane_entries << gs) < ml && (lr << (gs + 1)) <= nct) ++gs;
     if (lane == 0) w.lvl_nchunk[lev] = e | (gs << 28);
   }
   __syncthreads();
@@ -965,36 +971,36 @@ __device__ int build_stream(const Walker& w, const Params& P, bool upper, int nl
       while (gw > 0 && (lr << gw) > 32) --gw;
       const int wmode = (!expanded && lr <= P.warp_rows && (lr << gw) <= 32) ? gw + 1 : 0;
       const int lgs = gsl | (wmode << 8);
-      if (cs < kMaxSeg && chunk_bytes(cs + 1, cr + lr, ce + le, tsz, with_dv) <= SB) {
+      if (cs < kMaxSeg && cbytes(cs + 1, cr + lr, ce + le) <= SB) {
         w.seg_meta[nseg++] = make_int4(q, lr, le, lgs);  // the whole level joins the open chunk
         ++cs; cr += lr; ce += le;
         continue;
       }
       while (q < qe) {  // close the open chunk if any, then pieces of this level
-        if (cs > 0 && (cs == kMaxSeg || chunk_bytes(cs + 1, cr + 1, ce + len[rows[q]], tsz, with_dv) > SB)) {
+        if (cs > 0 && (cs == kMaxSeg || cbytes(cs + 1, cr + 1, ce + len[rows[q]]) > SB)) {
           w.chunk_meta[nch] = make_int4(c_seg0, cs, cr, ce);
-          w.lvl_cur[nch] = chunk_bytes(cs, cr, ce, tsz, with_dv);
+          w.lvl_cur[nch] = cbytes(cs, cr, ce);
           ++nch; c_seg0 = nseg; cs = 0; cr = 0; ce = 0;
         }
         const int q0 = q;
         int pr = 0, pe = 0;
         while (q < qe) {
           const int L = len[rows[q]];
-          if ((cr + pr) > 0 && chunk_bytes(cs + 1, cr + pr + 1, ce + pe + L, tsz, with_dv) > SB) break;
+          if ((cr + pr) > 0 && cbytes(cs + 1, cr + pr + 1, ce + pe + L) > SB) break;
           ++pr; pe += L; ++q;
         }
         w.seg_meta[nseg++] = make_int4(q0, pr, pe, lgs);
         ++cs; cr += pr; ce += pe;
         if (q < qe) {  // the slot is full: close it
           w.chunk_meta[nch] = make_int4(c_seg0, cs, cr, ce);
-          w.lvl_cur[nch] = chunk_bytes(cs, cr, ce, tsz, with_dv);
+          w.lvl_cur[nch] = cbytes(cs, cr, ce);
           ++nch; c_seg0 = nseg; cs = 0; cr = 0; ce = 0;
         }
       }
     }
     if (cs > 0) {
       w.chunk_meta[nch] = make_int4(c_seg0, cs, cr, ce);
-      w.lvl_cur[nch] = chunk_bytes(cs, cr, ce, tsz, with_dv);
+      w.lvl_cur[nch] = cbytes(cs, cr, ce);
       ++nch;
     }
     sh.iflag[2] = nch;
@@ -1007,6 +1013,56 @@ __device__ int build_stream(const Walker& w, const Params& P, bool upper, int nl
   for (int c = tid; c < nch_total; c += nt) tab[c].x = w.lvl_cur[c];
   __syncthreads();
   // fill the chunks, one warp per chunk
+  if (expanded) {
+    for (int c = wid; c < nch_total; c += nw) {
+      const int4 cm = w.chunk_meta[c];
+      const int seg0 = cm.x, nseg = cm.y, nr = cm.z, ne = cm.w;
+      unsigned char* base = stream + tab[c].x;
+      int4* seg = (int4*)(base + kChunkHdr);
+      int4* desc = (int4*)(base + kChunkHdr + 16 * nseg);
+      unsigned char* ent = base + kChunkHdr + 16 * nseg + 16 * nr;
+      if (lane == 0) *(int4*)base = make_int4(nseg, nr, ne, 1);
+      if (lane < kMaxSlots)
+        ((int2*)(base + 16))[lane] = c + 1 + lane < nch_total ? tab[c + 1 + lane] : make_int2(0, 0);
+      int rbase = 0, carry = 0;
+      for (int sgi = 0; sgi < nseg; ++sgi) {
+        const int4 sm = w.seg_meta[seg0 + sgi];
+        const int q0 = sm.x, sr = sm.y;
+        if (lane == 0) seg[sgi] = make_int4(rbase, sr, sm.w & 0xff, 0);
+        for (int b0 = 0; b0 < sr; b0 += 32) {
+          const int i = b0 + lane;
+          const int r = i < sr ? rows[q0 + i] : 0;
+          const int L = i < sr ? len[r] : 0;
+          int inc = L;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+          }
+          if (i < sr) desc[rbase + i] = make_int4(r, carry + inc - L, carry + inc, 0);
+          carry += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        rbase += sr;
+      }
+      __syncwarp();
+      for (int i = 0; i < nr; ++i) {
+        const int4 d = desc[i];
+        const int r = d.x, b = d.y, L = d.z - d.y;
+        for (int t = lane; t < L; t += 32) {
+          const int col = colv[(size_t)r * capLU + t];
+          const double val = valv[(size_t)r * capLU + t];
+          if (tsz == 4) {
+            reinterpret_cast<float2*>(ent)[b + t] = make_float2(__int_as_float(col), (float)val);
+          } else {
+            reinterpret_cast<int*>(ent)[b + t] = col;
+            reinterpret_cast<double*>(ent + pad16(4 * ne))[b + t] = val;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    return nch_total;
+  }
   for (int c = wid; c < nch_total; c += nw) {
     const int4 cm = w.chunk_meta[c];
     const int seg0 = cm.x, nseg = cm.y, nr = cm.z, ne = cm.w;
@@ -1249,7 +1305,12 @@ __device__ __noinline__ void relabel_and_levels(const Walker& w, const Params& P
     ncu = build_stream<T>(w, P, true, nlu, sh);
     if (tid == 0) { w.ctl->ngrp_l = nll; w.ctl->ngrp_u = nlu; }
   }
-  if (tid == 0) { w.ctl->nchunk_l = ncl; w.ctl->nchunk_u = ncu; }
+  if (tid == 0) {
+    w.ctl->nchunk_l = ncl;
+    w.ctl->nchunk_u = ncu;
+    w.ctl->stream_bytes = (ncl ? (long long)w.lchunk[ncl - 1].x + w.lchunk[ncl - 1].y : 0) +
+                          (ncu ? (long long)w.uchunk[ncu - 1].x + w.uchunk[ncu - 1].y : 0);
+  }
   fence_proxy_async_global();  // the streams are read next by bulk (async-proxy) copies
   __syncthreads();
 }

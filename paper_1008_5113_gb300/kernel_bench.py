@@ -34,6 +34,7 @@ def main(argv=None):
     ap.add_argument("--sweeps", type=int, default=0, help="dense-engine sweeps before the factorisation")
     ap.add_argument("--lfil", type=int, default=-1)
     ap.add_argument("--group", type=int, default=8, help="trisolve_group (1: level by level)")
+    ap.add_argument("--row-cap", type=int, default=0, help="trisolve_row_cap (0: the default)")
     args = ap.parse_args(argv)
 
     import numpy as np
@@ -57,7 +58,8 @@ def main(argv=None):
         state = np.concatenate([vmc.vmc_get_positions(ctxd, w).reshape(-1) for w in range(args.walkers)])
         vmc.vmc_destroy(ctxd)
     ctx = vmc.vmc_create(systems, vmc.params(precision=args.precision, lfil_extra=args.lfil,
-                                             trisolve_group=args.group), stream=stream)
+                                             trisolve_group=args.group, trisolve_row_cap=args.row_cap),
+                         stream=stream)
     try:
         if state is None:
             vmc.vmc_init_positions(ctx, seeds, 0.1)
@@ -78,8 +80,9 @@ def main(argv=None):
         st = [vmc.vmc_get_stats(ctx, w) for w in range(args.walkers)]
         by = sum(s["alg_bytes"] for s in st)
         out = {"kernel": args.which, "n": args.K ** 3, "walkers": args.walkers, "precision": args.precision,
-               "state_sweeps": args.sweeps, "lfil": args.lfil, "group": args.group,
+               "state_sweeps": args.sweeps, "lfil": args.lfil, "group": args.group, "row_cap": args.row_cap,
                "levels": (st[0]["levels_L"], st[0]["levels_U"]), "groups": (st[0]["groups_L"], st[0]["groups_U"]),
+               "stream_bytes": st[0]["stream_bytes"],
                "us_per_apply": 1000.0 * ms / args.reps, "bytes_per_apply": by / args.reps,
                "gbs": by / (ms / 1000.0) / 1e9, "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
         print(json.dumps(out), flush=True)

@@ -47,7 +47,8 @@ class vmc_solver_params(C.Structure):
                 ("refactor_reorder", C.c_int), ("trisolve", C.c_int),
                 ("graphs", C.c_int), ("trigger_rtol", C.c_double), ("trigger_its", C.c_int), ("sweep_moves", C.c_int),
                 ("ilutp_variant", C.c_int), ("trisolve_warp_rows", C.c_int),
-                ("trisolve_group", C.c_int)]
+                ("trisolve_group", C.c_int), ("trisolve_row_cap", C.c_int),
+                ("trisolve_lane_entries", C.c_int)]
 
 
 class vmc_stats(C.Structure):
@@ -64,7 +65,7 @@ class vmc_stats(C.Structure):
                 ("async_wait_cycles", C.c_int64), ("async_factor_cycles", C.c_int64), ("factor_set", C.c_int),
                 ("async_lag", C.c_int), ("max_updates", C.c_int), ("groups_L", C.c_int), ("groups_U", C.c_int),
                 ("trigger_iterations", C.c_int64),
-                ("reorders_skipped", C.c_int64)]
+                ("reorders_skipped", C.c_int64), ("stream_bytes", C.c_int64)]
 
 
 class vmc_tune_trial(C.Structure):

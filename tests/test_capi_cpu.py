@@ -67,6 +67,12 @@ def test_create_rejects_invalid_params(vmc, field, value):
     assert e.value.status == 1
 
 
+def test_create_rejects_rows_longer_than_a_stream_slot(vmc):
+    with pytest.raises(vmc.VmcError) as e:
+        vmc.vmc_create([(6, 0, 1.0, 2.0, 1.5)], vmc.params(lfil_extra=1000))
+    assert e.value.status == 1 and "stream slot" in str(e.value)
+
+
 def test_null_arguments(vmc):
     lib = vmc.lib()
     assert lib.vmc_create(None, 1, None, None, None) == 1

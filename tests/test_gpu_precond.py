@@ -171,8 +171,9 @@ def test_grouped_triangular_solves_apply_the_same_preconditioner(vmc, hard_posit
     rng = np.random.default_rng(5)
     v = rng.standard_normal(1000)
     out = {}
-    for group in (1, 8):
-        ctx = vmc.vmc_create([(10, 0, 1.0, 2.0, 1.5)], vmc.params(precision=prec, trisolve_group=group))
+    for group, row_cap in ((1, 0), (8, 0), (16, 400)):
+        ctx = vmc.vmc_create([(10, 0, 1.0, 2.0, 1.5)], vmc.params(precision=prec, trisolve_group=group,
+                                                                  trisolve_row_cap=row_cap))
         try:
             vmc.vmc_set_positions(ctx, 0, R)
             L, U, perm = vmc.vmc_get_factors(ctx, 0)
@@ -180,9 +181,12 @@ def test_grouped_triangular_solves_apply_the_same_preconditioner(vmc, hard_posit
         finally:
             vmc.vmc_destroy(ctx)
     z1, L1, U1, s1 = out[1]
-    z8, L8, U8, s8 = out[8]
-    assert np.array_equal(L1, L8) and np.array_equal(U1, U8)
     tol = 1e-12 if prec == 0 else 1e-5
-    assert np.abs(z8 - z1).max() <= tol * np.abs(z1).max()
     assert s1["groups_L"] == s1["levels_L"] and s1["groups_U"] == s1["levels_U"]
-    assert s8["groups_L"] < s8["levels_L"] and s8["groups_U"] < s8["levels_U"]
+    for g in (8, 16):
+        zg, Lg, Ug, sg = out[g]
+        assert np.array_equal(L1, Lg) and np.array_equal(U1, Ug)
+        assert np.abs(zg - z1).max() <= tol * np.abs(z1).max()
+        assert sg["groups_L"] < sg["levels_L"] and sg["groups_U"] < sg["levels_U"]
+    # longer expanded rows and more levels a group: fewer groups
+    assert out[16][3]["groups_L"] + out[16][3]["groups_U"] < out[8][3]["groups_L"] + out[8][3]["groups_U"]
