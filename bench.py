@@ -322,7 +322,9 @@ def main():
                 base.max_updates, base.refactor_lag = 128, 0
             return base, []
         t1 = time.perf_counter()
-        p, trials = vmc.vmc_autotune(systems, base, seeds, JITTER, SIGMA, 64, stream=stream, xyz=state,
+        # trials as long as one timed step: shorter ones miss the in-line refactorisations that
+        # a chain of 64-128 updates brings every 100-200 moves, and favour the in-line layouts
+        p, trials = vmc.vmc_autotune(systems, base, seeds, JITTER, SIGMA, moves, stream=stream, xyz=state,
                                      sweep0=EQUIL_SWEEPS)
         log(f"autotune (precision {prec}): {len(trials)} trials in {time.perf_counter() - t1:.1f} s; picked engine "
             f"{p.engine}, {p.block_threads} threads, chain {p.max_updates}, lag {p.refactor_lag}, lfil {p.lfil_extra}")
@@ -592,7 +594,7 @@ def main():
                            f"{EQUIL_SWEEPS} discarded sweeps, restored before every step (restore untimed)",
                    "engine": f"persistent, {p64.block_threads} threads a walker CTA, chain {p64.max_updates}",
                    "gmres_m": 30, "ilutp": f"drop 1e-4, permtol 0.5, lfil {p64.lfil_extra}",
-                   "solver_layout": "autotuned from the saved state" if trials64 else "fixed (no autotune)",
+                   "solver_layout": f"autotuned from the saved state ({moves} moves a walker a trial)" if trials64 else "fixed (no autotune)",
                    "inner_rtol": 1e-10, "trigger_rtol": 1e-6,
                    "refactorisation": refactoring, "l2": "256 MB buffer written between timed steps",
                    "side_legs": f"mixed: {side_steps} timed + 1 warm-up restored steps (its own autotuned "
@@ -622,7 +624,7 @@ def main():
     if skipped:
         out["skipped_over_budget"] = skipped
     out["autotune_fp64"] = [{k: t[k] for k in ("engine", "block_threads", "max_updates", "refactor_lag",
-                                                  "lfil_extra", "ratios_per_s")} for t in trials64]
+                                                  "lfil_extra", "trisolve_group", "ratios_per_s")} for t in trials64]
     out.update(extra)
     if not args.no_cpu_baseline and world == 1 and not args.headline_only:  # host cores, N = 1 only
         try:

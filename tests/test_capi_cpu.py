@@ -42,6 +42,7 @@ def test_default_params(vmc):
     assert p.N_max == 100.0 and p.slow_factor == 4.0 and p.lfil_extra == -1
     assert p.precision == vmc.PREC_MIXED and p.engine == vmc.ENGINE_PERSISTENT
     assert p.max_updates == -1 and p.refactor_lag == -1 and p.graphs == 1 and p.trisolve == 0
+    assert p.trisolve_group == 8 and p.trisolve_row_cap == 0 and p.trisolve_lane_entries == 0
 
 
 @pytest.mark.parametrize("system,why", [
@@ -60,7 +61,9 @@ def test_create_rejects_invalid_systems(vmc, system, why):
 
 @pytest.mark.parametrize("field,value", [("gmres_m", 0), ("gmres_m", 41), ("max_updates", 129), ("max_updates", -2),
                                          ("block_threads", 100), ("block_threads", 1024), ("precision", 3),
-                                         ("engine", 7), ("drop_tol", -1.0)])
+                                         ("engine", 7), ("drop_tol", -1.0), ("trisolve_row_cap", 481),
+                                         ("trisolve_row_cap", -1), ("trisolve_lane_entries", 65),
+                                         ("trisolve_lane_entries", -1), ("trisolve_group", 65)])
 def test_create_rejects_invalid_params(vmc, field, value):
     with pytest.raises(vmc.VmcError) as e:
         vmc.vmc_create([(6, 0, 1.0, 2.0, 1.5)], vmc.params(**{field: value}))

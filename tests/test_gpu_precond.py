@@ -171,22 +171,30 @@ def test_grouped_triangular_solves_apply_the_same_preconditioner(vmc, hard_posit
     rng = np.random.default_rng(5)
     v = rng.standard_normal(1000)
     out = {}
-    for group, row_cap in ((1, 0), (8, 0), (16, 400)):
+    # (levels a group, expanded-row cap, entries a lane); the last two cases size the lane
+    # groups differently (level by level and grouped)
+    cases = ((1, 0, 0), (8, 0, 0), (16, 400, 0), (1, 0, 16), (8, 0, 1))
+    for case in cases:
+        group, row_cap, lane_entries = case
         ctx = vmc.vmc_create([(10, 0, 1.0, 2.0, 1.5)], vmc.params(precision=prec, trisolve_group=group,
-                                                                  trisolve_row_cap=row_cap))
+                                                                  trisolve_row_cap=row_cap,
+                                                                  trisolve_lane_entries=lane_entries))
         try:
             vmc.vmc_set_positions(ctx, 0, R)
             L, U, perm = vmc.vmc_get_factors(ctx, 0)
-            out[group] = (vmc.vmc_apply_preconditioner(ctx, 0, v), L, U, vmc.vmc_get_stats(ctx, 0))
+            out[case] = (vmc.vmc_apply_preconditioner(ctx, 0, v), L, U, vmc.vmc_get_stats(ctx, 0))
         finally:
             vmc.vmc_destroy(ctx)
-    z1, L1, U1, s1 = out[1]
+    z1, L1, U1, s1 = out[cases[0]]
     tol = 1e-12 if prec == 0 else 1e-5
     assert s1["groups_L"] == s1["levels_L"] and s1["groups_U"] == s1["levels_U"]
-    for g in (8, 16):
-        zg, Lg, Ug, sg = out[g]
+    for case in cases[1:]:
+        zg, Lg, Ug, sg = out[case]
         assert np.array_equal(L1, Lg) and np.array_equal(U1, Ug)
         assert np.abs(zg - z1).max() <= tol * np.abs(z1).max()
-        assert sg["groups_L"] < sg["levels_L"] and sg["groups_U"] < sg["levels_U"]
+        if case[0] > 1:
+            assert sg["groups_L"] < sg["levels_L"] and sg["groups_U"] < sg["levels_U"]
+            assert sg["stream_bytes"] > s1["stream_bytes"]  # the expanded rows are longer
     # longer expanded rows and more levels a group: fewer groups
-    assert out[16][3]["groups_L"] + out[16][3]["groups_U"] < out[8][3]["groups_L"] + out[8][3]["groups_U"]
+    s16, s8 = out[cases[2]][3], out[cases[1]][3]
+    assert s16["groups_L"] + s16["groups_U"] < s8["groups_L"] + s8["groups_U"]
