@@ -317,7 +317,7 @@ def main():
         if args.no_autotune:  # the layouts the autotuner picks for this workload (persistent, 256 threads)
             base.lfil_extra = 32
             if args.layout == "pairs":
-                base.max_updates, base.refactor_lag = 128, 64
+                base.max_updates, base.refactor_lag = 32, 16
             else:
                 base.max_updates, base.refactor_lag = 128, 0
             return base, []
